@@ -1,0 +1,212 @@
+/*
+ * dqj.h -- C ABI of libdqj, a GB300 (sm_103a) renderer for isosurfaces of 3-D
+ * slices of dual-quaternion Julia sets (Kenwright, "Dual-Quaternion Julia
+ * Fractals").
+ *
+ * Method (paper references by section / equation):
+ *   - zeta_{n+1} = zeta_n^2 + c in 8-component dual-quaternion algebra
+ *     (Method, "Dual-Quaternion Julia Sets", Eq. dqjulia2; products from the
+ *     appendix, "Dual-Quaternion Operations");
+ *   - a sample escapes at the first n with modulus > R^2, and counts as inside
+ *     when it has not escaped after max_iter steps (Method, "Practical
+ *     Considerations");
+ *   - the 8-D space is cut by a 3-D slice, five coordinates held fixed
+ *     (Method, "Dimension Reduction");
+ *   - each pixel's ray is marched through a bounding box, the first inside
+ *     sample refined by bisection (Method, "Ray-Marching"); a normal comes from
+ *     central differences of neighbouring samples (Method,
+ *     "Lighting/Illumination") and is shaded with the ambient and diffuse terms
+ *     of Eq. phong.
+ *
+ * All functions return a dqj_status; no C++ exception crosses this boundary.
+ * On a non-OK status, dqj_last_error() returns a message for the calling thread.
+ * Functions are thread-safe unless stated otherwise.
+ */
+#ifndef DQJ_H
+#define DQJ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DQJ_ABI_VERSION 1
+
+typedef struct dqj_ctx dqj_ctx;
+typedef uint64_t dqj_ticket;
+
+typedef enum {
+    DQJ_OK = 0,
+    DQJ_ERR_INVALID = 1,   /* bad argument or parameter block                      */
+    DQJ_ERR_NOMEM = 2,     /* device or host allocation failed                     */
+    DQJ_ERR_BUSY = 3,      /* serving queue full (max_pending reached)             */
+    DQJ_ERR_TIMEOUT = 4,   /* a bounded wait ran out                               */
+    DQJ_ERR_CUDA = 5,      /* a CUDA runtime call failed; message has the detail   */
+    DQJ_ERR_NOT_FOUND = 6, /* unknown or already consumed ticket                   */
+    DQJ_ERR_CANCELLED = 7  /* request cancelled by dqj_destroy                     */
+} dqj_status;
+
+/* dqj_params.precision */
+enum {
+    DQJ_FP32 = 0,         /* FP32 throughout                                         */
+    DQJ_FP32_RECHECK = 1, /* FP32, samples within recheck_margin of R^2 re-evaluated
+                             in FP64 on the GPU; a pixel whose FP64 decision differs
+                             is re-rendered in FP64                                  */
+    DQJ_FP64 = 2          /* FP64 throughout                                         */
+};
+
+/* dqj_params.square_mode (Method, "Dual-Quaternion Julia Sets") */
+enum {
+    DQJ_SQUARE_ALGEBRAIC = 0,          /* zeta^2 = q_r^2 + (q_r q_d + q_d q_r) eps   */
+    DQJ_SQUARE_PAPER_COMPONENTWISE = 1 /* zeta^2 = q_r^2 + q_d^2 eps, as printed     */
+};
+
+/* dqj_params.modulus_mode (Introduction; appendix, magnitude) */
+enum {
+    DQJ_MODULUS_EUCLID8 = 0, /* |q_r|^2 + |q_d|^2                                   */
+    DQJ_MODULUS_DUALNUM = 1  /* |q_r|^2, the dual-number modulus of zeta zeta*      */
+};
+
+/* Per-context configuration for dqj_create. */
+typedef struct {
+    int32_t device;            /* CUDA device ordinal                                   */
+    uint64_t mem_budget_bytes; /* serving: device bytes admitted requests may occupy
+                                  (outputs the library allocates + scratch); 0 = 16 GiB */
+    int32_t max_pending;       /* serving: host queue bound; 0 = 4096                   */
+    const char *autotune_cache;/* path of the tile-shape cache (JSON) or NULL: the
+                                  env var DQJ_AUTOTUNE_CACHE, else built-in defaults    */
+} dqj_config;
+
+/*
+ * One render request.  Every length is in scene units, angles in degrees.
+ * Dual quaternions are 8 doubles (q_r | q_d), scalar first in each half
+ * (appendix, quaternion definition).
+ */
+typedef struct {
+    double c[8];                /* Julia constant (Eq. dqjulia2)                      */
+    double slice_origin[8];     /* 8-D point the 3-D slice passes through             */
+    double slice_basis[3][8];   /* orthonormal 3-frame: scene x,y,z -> R^8
+                                   ("Dimension Reduction"); orthonormal to 1e-9       */
+    double eye[3], target[3], up[3];
+    double fov_y_deg;           /* vertical field of view, 0 < fov < 180              */
+    int32_t width, height;      /* 1..16384 each                                      */
+    int32_t max_iter;           /* 1..1024 ("Practical Considerations")               */
+    double escape_radius;       /* R > 0; escape when modulus > R^2 (strict)          */
+    int32_t march_steps;        /* N in 1..65535: samples t_in + k (t_out-t_in)/N,
+                                   k = 0..N, over the ray's part inside the box       */
+    int32_t bisect_steps;       /* B in 0..30 halvings of the first crossing          */
+    double normal_h;            /* central-difference step h > 0                      */
+    double box_min[3], box_max[3]; /* march volume, box_min < box_max                 */
+    double light_dir[3];        /* direction to the light (normalised internally)     */
+    double k_ambient, k_diffuse;/* Eq. phong coefficients                             */
+    double albedo[3];           /* per-channel factor in [0, 1]                       */
+    int32_t precision;          /* DQJ_FP32 | DQJ_FP32_RECHECK | DQJ_FP64             */
+    double recheck_margin;      /* DQJ_FP32_RECHECK: |modulus - R^2| <= margin * R^2
+                                   marks a sample for FP64 re-evaluation; 0..0.5      */
+    int32_t square_mode;        /* DQJ_SQUARE_*                                       */
+    int32_t modulus_mode;       /* DQJ_MODULUS_*                                      */
+} dqj_params;
+
+/*
+ * Output planes, row-major with a row pitch in pixels (>= width).  Pixel (x, y)
+ * lives at element y * pitch_px + x; normal holds 3 floats and rgba 4 bytes per
+ * pixel at 3x / 4x that element offset.  For dqj_render / dqj_submit these are
+ * DEVICE pointers owned by the caller, valid until the render completes; for
+ * dqj_render_host they are HOST pointers.  Any plane may be NULL (not written).
+ *
+ *   iter   hit: escape count of the final outside bisection end (max_iter when
+ *          the first march sample is inside); miss: largest escape count over
+ *          the march samples (0 when the ray misses the box)
+ *   depth  ray parameter of the hit (midpoint of the final bracket), +inf on miss
+ *   normal unit normal (+gradient of the modulus field), (0,0,0) on miss
+ *   rgba   shaded colour, alpha 255 on hit; (0,0,0,0) on miss
+ *   stats  optional DEVICE (render) / HOST (render_host) array of DQJ_NSTATS
+ *          int64 counters, overwritten with this render's counts
+ */
+typedef struct {
+    int32_t *iter;
+    float *depth;
+    float *normal;
+    uint8_t *rgba;
+    int64_t pitch_px;
+    int64_t *stats;
+} dqj_outputs;
+
+/* Indices into dqj_outputs.stats. */
+enum {
+    DQJ_STAT_CLASS_ITERS = 0,  /* DQ iterations of march + bisection samples          */
+    DQJ_STAT_NORMAL_ITERS = 1, /* DQ iterations of the six normal evaluations         */
+    DQJ_STAT_SAMPLES = 2,      /* classified samples (march + bisection)              */
+    DQJ_STAT_HITS = 3,         /* pixels with an inside march sample                  */
+    DQJ_STAT_RECHECKS = 4,     /* samples re-evaluated in FP64                        */
+    DQJ_STAT_FIXUPS = 5,       /* pixels re-rendered in FP64 after a disagreement     */
+    DQJ_STAT_FIXUP_ITERS = 6,  /* DQ iterations spent by those re-renders             */
+    DQJ_STAT_OVERFLOW = 7,     /* recheck-queue overflows (pixel re-rendered instead) */
+    DQJ_STAT_MARCH_ITERS = 8,  /* part of CLASS_ITERS spent by march samples          */
+    DQJ_STAT_RESERVED = 9,
+    DQJ_NSTATS = 10
+};
+
+/* Fill *p with the defaults of the single-frame scene: c = (-0.2, 0.6, 0.2, 0.2 |
+ * 0.1, 0, 0, 0.05), real-quaternion coordinates 0..2 free, 256x256, max_iter 12,
+ * R = 4, N = 256, B = 8, h = 1e-4, box [-2,2]^3, eye (0,0,3.5) looking at the
+ * origin, up +y, fov 45, light (1,1,1), k_a 0.15, k_d 0.85, white albedo,
+ * DQJ_FP32, margin 1e-3, algebraic square, EUCLID8 modulus. */
+dqj_status dqj_default_params(dqj_params *p);
+
+/* Check a parameter block on the host (no device needed).  DQJ_ERR_INVALID
+ * with a message naming the first offending field. */
+dqj_status dqj_validate_params(const dqj_params *p);
+
+/* Create a context on cfg->device (NULL cfg: device 0, defaults).  The context
+ * owns its scratch memory, streams and the serving thread. */
+dqj_status dqj_create(const dqj_config *cfg, dqj_ctx **out);
+
+/* Enqueue one frame on cuda_stream (a cudaStream_t; NULL = legacy default) and
+ * return without waiting.  Outputs are caller-owned device memory.  Renders on one
+ * context are ordered with each other across streams (they share scratch). */
+dqj_status dqj_render(dqj_ctx *ctx, const dqj_params *p, const dqj_outputs *out, void *cuda_stream);
+
+/* Render one frame into HOST buffers: the library renders into context-owned
+ * device planes, copies the requested planes to the host and waits.  Blocking. */
+dqj_status dqj_render_host(dqj_ctx *ctx, const dqj_params *p, const dqj_outputs *host_out);
+
+/* Serving: queue a request and return a ticket at once.  Outputs are
+ * caller-owned device memory that must stay valid until dqj_poll reports done.
+ * Requests are admitted to the GPU while their footprint fits the context's
+ * memory budget; admitted requests run together in one persistent launch.
+ * DQJ_ERR_BUSY when max_pending requests are queued and not yet admitted. */
+dqj_status dqj_submit(dqj_ctx *ctx, const dqj_params *p, const dqj_outputs *out, dqj_ticket *ticket);
+
+/* Non-blocking completion check.  *done = 1 and *result = the request's status
+ * once finished; the ticket is then consumed (a second poll: DQJ_ERR_NOT_FOUND). */
+dqj_status dqj_poll(dqj_ctx *ctx, dqj_ticket ticket, int *done, dqj_status *result);
+
+/* Cancel queued requests, wait (bounded) for admitted ones, free everything. */
+dqj_status dqj_destroy(dqj_ctx *ctx);
+
+/* Profiling: with ring_frames > 0 (at most 4096), every later render on this
+ * context records CUDA events on its own stream before its first pass and after
+ * each pass, into a ring that keeps the last ring_frames renders; 0 turns this
+ * off.  dqj_pass_ms waits for the `frames` most recent recorded renders (oldest
+ * first, frames <= ring_frames) and writes 4 floats per render: elapsed ms of
+ * the march, of bisection + normal + shading, of the FP64 recheck and of the
+ * FP64 re-render (0 for passes that did not run).  DQJ_ERR_NOT_FOUND when fewer
+ * renders were recorded. */
+dqj_status dqj_set_profiling(dqj_ctx *ctx, int32_t ring_frames);
+dqj_status dqj_pass_ms(dqj_ctx *ctx, int32_t frames, float *ms);
+
+/* Message for the last non-OK status on this thread ("" if none). */
+const char *dqj_last_error(void);
+
+/* Measurement: FP32 FMA throughput of this GPU with independent dependency
+ * chains.  variant 0 = scalar fma.rn.f32, 1 = paired fma.rn.f32x2.  Runs
+ * `launches` timed launches on device `device`; *flops_per_s gets the best. */
+dqj_status dqj_fma_peak(int32_t device, int32_t variant, int32_t launches, double *flops_per_s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DQJ_H */

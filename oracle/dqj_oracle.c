@@ -40,7 +40,9 @@
  *    bisection steps refine the crossing.
  *  - Normal (Method, "Lighting/Illumination"): central differences of the scalar
  *    field F(p) = modulus(zeta_{n*}(p)) along the scene axes, n* the escape count
- *    of the final outside bisection end, iterated exactly n* times.
+ *    of the final outside bisection end, iterated exactly n* times.  When any of
+ *    the six values exceeds 2^100 or is not finite (a neighbour that escaped
+ *    long before n*), or the gradient is zero, the normal is -d.
  *  - Shading (Eq. phong): ambient plus diffuse terms only.
  */
 #include <math.h>
@@ -371,6 +373,10 @@ static double normal_field(const or_scene *s, const double *p, int n, int64_t *i
     return or_modulus(zn, s->modulus_mode);
 }
 
+/* Largest normal-field value used for a gradient: 2^100 (exact in float and
+ * double).  Larger or non-finite values select the fallback normal -d. */
+#define NORMAL_FMAX 1267650600228229401496703205376.0
+
 /* ------------------------------------------------------------------------- */
 /* One pixel: camera ray, box clip, march, bisection, normal, shading.        */
 /* ------------------------------------------------------------------------- */
@@ -461,8 +467,11 @@ static void render_pixel(const or_scene *s, int i, int j, pixel_out *po, or_trac
     po->iter = n_star;
     po->depth = t.depth;
 
-    /* Normal: central differences of F along the scene axes. */
+    /* Normal: central differences of F along the scene axes.  Overflow guard
+     * (the paper gives none): when any of the six field values exceeds
+     * NORMAL_FMAX = 2^100 or is not finite, the normal is -d. */
     double ph[3], g[3];
+    int guard = 0;
     ray_point(t.o, t.d, t.depth, ph);
     for (int a = 0; a < 3; ++a) {
         double pp[3] = {ph[0], ph[1], ph[2]};
@@ -471,10 +480,11 @@ static void render_pixel(const or_scene *s, int i, int j, pixel_out *po, or_trac
         pm[a] -= s->normal_h;
         double fp = normal_field(s, pp, n_star, &t.normal_iters);
         double fm = normal_field(s, pm, n_star, &t.normal_iters);
+        if (!(fp <= NORMAL_FMAX) || !(fm <= NORMAL_FMAX)) guard = 1;
         g[a] = fp - fm;
     }
     double gl = sqrt(v3_dot(g, g));
-    if (!(gl > 0.0) || !isfinite(gl)) {
+    if (guard || !(gl > 0.0)) {
         po->normal[0] = -t.d[0];
         po->normal[1] = -t.d[1];
         po->normal[2] = -t.d[2];

@@ -1,0 +1,88 @@
+// dqj_internal.h -- structures shared by the host runtime and the CUDA kernels
+// of libdqj.  Not part of the public ABI (include/dqj.h).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace dqj {
+
+// Per-frame constants derived on the host in double, stored in the precision the
+// kernel computes in.  Passed by value as a kernel parameter, so the kernels read
+// them straight from the constant bank.
+template <typename T>
+struct FrameT {
+    T c[8];        // Julia constant (q_r | q_d)
+    T A[8];        // slice_origin + E * eye: slice image of the camera position
+    T O[8];        // slice_origin
+    T E[3][8];     // slice frame, scene axis a -> R^8
+    T eye[3];
+    T fwd[3], right[3], upv[3];
+    T th, aspect;  // tan(fov_y / 2), width / height (FP64 camera formula)
+    T sxa, sxb;    // FP32 camera: sx = (x + 0.5) * sxa + sxb
+    T sya, syb;    //              sy = (y + 0.5) * sya + syb
+    T bmin[3], bmax[3];
+    T R2;          // escape threshold on the modulus, R^2
+    T margin;      // recheck band: |modulus - R^2| <= margin (= recheck_margin * R^2)
+    T h;           // normal step
+    T light[3];    // unit vector to the light
+    T ka, kd, albedo[3];
+};
+
+// Encoding of a queued FP64 recheck: which sample of which pixel.
+//   b == kMarchSample : march sample t_in + k * delta
+//   b <  kMarchSample : bisection sample at level b of bracket (k-1, k);
+//                       bit i of path = 1 when level i moved lo up to mid
+constexpr int kMarchSample = 31;
+
+struct FrameDesc {
+    FrameT<float> f;
+    FrameT<double> d;
+    int32_t W, H, max_iter, N, B;
+    int32_t square_mode, modulus_mode, precision;
+    int32_t tile_w, tile_h, tiles_x, tiles_y;
+    int64_t pitch;
+    int32_t *iter;
+    float *depth;
+    float *normal;
+    uint8_t *rgba;
+    uint32_t epoch;   // tag for per-pixel dirty flags, changes every frame
+    uint32_t pad;
+};
+
+// Counters at the head of the scratch block; zeroed before every frame.
+struct Counters {
+    unsigned long long stats[10]; // DQJ_STAT_* order
+    unsigned int tile_next;       // next tile to claim in the march
+    unsigned int hit_count;       // entries in the hit list
+    unsigned int hit_next;        // next hit entry to claim in the bisection pass
+    unsigned int queue_count;     // entries pushed to the recheck queue (may exceed cap)
+    unsigned int queue_next;
+    unsigned int dirty_count;     // pixels to re-render in FP64
+    unsigned int dirty_next;
+    unsigned int pad[5];
+};
+static_assert(sizeof(Counters) == 128, "Counters layout");
+
+// Views into one scratch allocation owned by a context.
+struct Scratch {
+    Counters *ctr;
+    int4 *hits;           // {pixel, k_first, n_prev, 0}
+    uint32_t hit_cap;
+    int4 *queue;          // {pixel, k | b << 16, path, n32}
+    uint32_t queue_cap;
+    uint32_t *dirty_flag; // per pixel, == epoch when the pixel is queued for re-render
+    int32_t *dirty_list;
+    uint32_t dirty_cap;
+};
+
+// Host-side launch helpers implemented in render.cu.
+// Enqueue the passes of one frame on st.  ev (optional, 5 events) is recorded
+// before the march and after the march, bisect, recheck and fixup passes.
+cudaError_t launch_frame(const FrameDesc &fd, const Scratch &sc, cudaStream_t st, int num_sms,
+                         cudaEvent_t *ev = nullptr);
+cudaError_t fma_peak_launch(int variant, int num_sms, float *sink, cudaStream_t st, double *flops);
+
+}  // namespace dqj

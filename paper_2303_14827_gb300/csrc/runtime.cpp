@@ -1,0 +1,492 @@
+// runtime.cpp -- C ABI entry points, parameter validation, per-frame constants
+// and scratch management of libdqj.
+#include "runtime.h"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+namespace dqj {
+
+static thread_local std::string g_err;
+
+dqj_status fail(dqj_status st, const std::string &msg)
+{
+    g_err = msg;
+    return st;
+}
+
+dqj_status cuda_fail(cudaError_t e, const char *what)
+{
+    g_err = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return e == cudaErrorMemoryAllocation ? DQJ_ERR_NOMEM : DQJ_ERR_CUDA;
+}
+
+static bool finite_all(const double *v, int n)
+{
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(v[i])) return false;
+    return true;
+}
+
+dqj_status validate(const dqj_params *p)
+{
+    if (!p) return fail(DQJ_ERR_INVALID, "params is NULL");
+    if (p->width < 1 || p->width > 16384) return fail(DQJ_ERR_INVALID, "width must be in 1..16384");
+    if (p->height < 1 || p->height > 16384) return fail(DQJ_ERR_INVALID, "height must be in 1..16384");
+    if (p->max_iter < 1 || p->max_iter > 1024) return fail(DQJ_ERR_INVALID, "max_iter must be in 1..1024");
+    if (!(p->escape_radius > 0.0) || !std::isfinite(p->escape_radius))
+        return fail(DQJ_ERR_INVALID, "escape_radius must be finite and > 0");
+    if (p->march_steps < 1 || p->march_steps > 65535) return fail(DQJ_ERR_INVALID, "march_steps must be in 1..65535");
+    if (p->bisect_steps < 0 || p->bisect_steps > 30) return fail(DQJ_ERR_INVALID, "bisect_steps must be in 0..30");
+    if (!(p->fov_y_deg > 0.0 && p->fov_y_deg < 180.0)) return fail(DQJ_ERR_INVALID, "fov_y_deg must be in (0, 180)");
+    if (!(p->normal_h > 0.0) || !std::isfinite(p->normal_h))
+        return fail(DQJ_ERR_INVALID, "normal_h must be finite and > 0");
+    if (p->precision < DQJ_FP32 || p->precision > DQJ_FP64)
+        return fail(DQJ_ERR_INVALID, "precision must be DQJ_FP32, DQJ_FP32_RECHECK or DQJ_FP64");
+    if (!(p->recheck_margin >= 0.0 && p->recheck_margin <= 0.5))
+        return fail(DQJ_ERR_INVALID, "recheck_margin must be in [0, 0.5]");
+    if (p->square_mode < 0 || p->square_mode > 1) return fail(DQJ_ERR_INVALID, "square_mode must be 0 or 1");
+    if (p->modulus_mode < 0 || p->modulus_mode > 1) return fail(DQJ_ERR_INVALID, "modulus_mode must be 0 or 1");
+    if (!finite_all(p->c, 8)) return fail(DQJ_ERR_INVALID, "c must be finite");
+    if (!finite_all(p->slice_origin, 8)) return fail(DQJ_ERR_INVALID, "slice_origin must be finite");
+    if (!finite_all(&p->slice_basis[0][0], 24)) return fail(DQJ_ERR_INVALID, "slice_basis must be finite");
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            double dot = 0.0;
+            for (int i = 0; i < 8; ++i) dot += p->slice_basis[a][i] * p->slice_basis[b][i];
+            if (std::fabs(dot - (a == b ? 1.0 : 0.0)) > 1e-9)
+                return fail(DQJ_ERR_INVALID, "slice_basis rows must be orthonormal (to 1e-9)");
+        }
+    if (!finite_all(p->eye, 3) || !finite_all(p->target, 3) || !finite_all(p->up, 3))
+        return fail(DQJ_ERR_INVALID, "eye, target and up must be finite");
+    double f[3] = {p->target[0] - p->eye[0], p->target[1] - p->eye[1], p->target[2] - p->eye[2]};
+    const double fl = std::sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+    if (!(fl > 0.0)) return fail(DQJ_ERR_INVALID, "eye and target must differ");
+    const double cx = f[1] * p->up[2] - f[2] * p->up[1], cy = f[2] * p->up[0] - f[0] * p->up[2],
+                 cz = f[0] * p->up[1] - f[1] * p->up[0];
+    const double ul = std::sqrt(p->up[0] * p->up[0] + p->up[1] * p->up[1] + p->up[2] * p->up[2]);
+    if (!(std::sqrt(cx * cx + cy * cy + cz * cz) > 1e-12 * fl * ul))
+        return fail(DQJ_ERR_INVALID, "up must not be parallel to the view direction");
+    if (!finite_all(p->box_min, 3) || !finite_all(p->box_max, 3)) return fail(DQJ_ERR_INVALID, "box must be finite");
+    for (int a = 0; a < 3; ++a)
+        if (!(p->box_min[a] < p->box_max[a])) return fail(DQJ_ERR_INVALID, "box_min must be < box_max");
+    if (!finite_all(p->light_dir, 3)) return fail(DQJ_ERR_INVALID, "light_dir must be finite");
+    if (!(p->light_dir[0] * p->light_dir[0] + p->light_dir[1] * p->light_dir[1] + p->light_dir[2] * p->light_dir[2] >
+          0.0))
+        return fail(DQJ_ERR_INVALID, "light_dir must be non-zero");
+    if (!std::isfinite(p->k_ambient) || !std::isfinite(p->k_diffuse))
+        return fail(DQJ_ERR_INVALID, "k_ambient and k_diffuse must be finite");
+    for (int a = 0; a < 3; ++a)
+        if (!(p->albedo[a] >= 0.0 && p->albedo[a] <= 1.0)) return fail(DQJ_ERR_INVALID, "albedo must be in [0, 1]");
+    return DQJ_OK;
+}
+
+template <typename T>
+static void cast_frame(const FrameT<double> &d, FrameT<T> &f)
+{
+    const double *src = reinterpret_cast<const double *>(&d);
+    T *dst = reinterpret_cast<T *>(&f);
+    static_assert(sizeof(FrameT<double>) % sizeof(double) == 0, "FrameT is an array of doubles");
+    for (size_t i = 0; i < sizeof(FrameT<double>) / sizeof(double); ++i) dst[i] = (T)src[i];
+}
+
+void derive_frame(const dqj_params &p, FrameDesc &fd, int tile_w, int tile_h)
+{
+    std::memset(&fd, 0, sizeof fd);
+    FrameT<double> &F = fd.d;
+    for (int i = 0; i < 8; ++i) {
+        F.c[i] = p.c[i];
+        F.O[i] = p.slice_origin[i];
+        for (int a = 0; a < 3; ++a) F.E[a][i] = p.slice_basis[a][i];
+        F.A[i] = p.slice_origin[i] + p.eye[0] * p.slice_basis[0][i] + p.eye[1] * p.slice_basis[1][i] +
+                 p.eye[2] * p.slice_basis[2][i];
+    }
+    double f[3], r[3], u[3];
+    for (int a = 0; a < 3; ++a) f[a] = p.target[a] - p.eye[a];
+    double fl = std::sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+    for (int a = 0; a < 3; ++a) f[a] /= fl;
+    r[0] = f[1] * p.up[2] - f[2] * p.up[1];
+    r[1] = f[2] * p.up[0] - f[0] * p.up[2];
+    r[2] = f[0] * p.up[1] - f[1] * p.up[0];
+    double rl = std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    for (int a = 0; a < 3; ++a) r[a] /= rl;
+    u[0] = r[1] * f[2] - r[2] * f[1];
+    u[1] = r[2] * f[0] - r[0] * f[2];
+    u[2] = r[0] * f[1] - r[1] * f[0];
+    for (int a = 0; a < 3; ++a) {
+        F.eye[a] = p.eye[a];
+        F.fwd[a] = f[a];
+        F.right[a] = r[a];
+        F.upv[a] = u[a];
+        F.bmin[a] = p.box_min[a];
+        F.bmax[a] = p.box_max[a];
+        F.albedo[a] = p.albedo[a];
+    }
+    F.th = std::tan(0.5 * p.fov_y_deg * (M_PI / 180.0));
+    F.aspect = (double)p.width / (double)p.height;
+    F.sxa = 2.0 * F.th * F.aspect / (double)p.width;
+    F.sxb = -F.th * F.aspect;
+    F.sya = -2.0 * F.th / (double)p.height;
+    F.syb = F.th;
+    F.R2 = p.escape_radius * p.escape_radius;
+    F.margin = p.recheck_margin * F.R2;
+    F.h = p.normal_h;
+    const double ll = std::sqrt(p.light_dir[0] * p.light_dir[0] + p.light_dir[1] * p.light_dir[1] +
+                                p.light_dir[2] * p.light_dir[2]);
+    for (int a = 0; a < 3; ++a) F.light[a] = p.light_dir[a] / ll;
+    F.ka = p.k_ambient;
+    F.kd = p.k_diffuse;
+    cast_frame<float>(F, fd.f);
+    fd.W = p.width;
+    fd.H = p.height;
+    fd.max_iter = p.max_iter;
+    fd.N = p.march_steps;
+    fd.B = p.bisect_steps;
+    fd.square_mode = p.square_mode;
+    fd.modulus_mode = p.modulus_mode;
+    fd.precision = p.precision;
+    fd.tile_w = tile_w;
+    fd.tile_h = tile_h;
+    fd.tiles_x = (p.width + tile_w - 1) / tile_w;
+    fd.tiles_y = (p.height + tile_h - 1) / tile_h;
+}
+
+static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+void scratch_free(ScratchBuf &s)
+{
+    if (s.base) cudaFree(s.base);
+    s = ScratchBuf{};
+}
+
+dqj_status scratch_ensure(ScratchBuf &s, uint64_t pixels, bool need_queue)
+{
+    if (s.base && pixels <= s.pixels && (!need_queue || s.with_queue)) return DQJ_OK;
+    const uint64_t px = std::max<uint64_t>(pixels, s.pixels);
+    const bool wq = need_queue || s.with_queue;
+    const uint64_t qcap = wq ? 4 * px : 0;
+    size_t off = 0;
+    const size_t o_ctr = off;
+    off = align_up(off + sizeof(Counters), 256);
+    const size_t o_hits = off;
+    off = align_up(off + px * sizeof(int4), 256);
+    const size_t o_queue = off;
+    off = align_up(off + qcap * sizeof(int4), 256);
+    const size_t o_flag = off;
+    off = align_up(off + px * sizeof(uint32_t), 256);
+    const size_t o_list = off;
+    off = align_up(off + px * sizeof(int32_t), 256);
+    void *base = nullptr;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "scratch: synchronize");
+    if (s.base) cudaFree(s.base);
+    s = ScratchBuf{};
+    e = cudaMalloc(&base, off);
+    if (e != cudaSuccess) return cuda_fail(e, "scratch: cudaMalloc");
+    e = cudaMemset(base, 0, off);
+    if (e != cudaSuccess) {
+        cudaFree(base);
+        return cuda_fail(e, "scratch: cudaMemset");
+    }
+    char *b = static_cast<char *>(base);
+    s.base = base;
+    s.bytes = off;
+    s.pixels = (uint32_t)px;
+    s.with_queue = wq;
+    s.epoch = 0;
+    s.view.ctr = reinterpret_cast<Counters *>(b + o_ctr);
+    s.view.hits = reinterpret_cast<int4 *>(b + o_hits);
+    s.view.hit_cap = (uint32_t)px;
+    s.view.queue = wq ? reinterpret_cast<int4 *>(b + o_queue) : nullptr;
+    s.view.queue_cap = (uint32_t)qcap;
+    s.view.dirty_flag = reinterpret_cast<uint32_t *>(b + o_flag);
+    s.view.dirty_list = reinterpret_cast<int32_t *>(b + o_list);
+    s.view.dirty_cap = (uint32_t)px;
+    return DQJ_OK;
+}
+
+// Tile shape of a frame: the autotuned one for its class, else 8 x 4.
+static void pick_tile(dqj_ctx *ctx, const dqj_params &p, int &tw, int &th)
+{
+    tw = 8;
+    th = 4;
+    const int64_t px = (int64_t)p.width * p.height;
+    const int cls = px <= 65536 ? 0 : px <= 262144 ? 1 : px <= 1048576 ? 2 : 3;
+    const int key = cls * 4 + (p.max_iter <= 12 ? 0 : p.max_iter <= 20 ? 1 : p.max_iter <= 28 ? 2 : 3);
+    auto it = ctx->tiles.find(key);
+    if (it != ctx->tiles.end()) {
+        tw = it->second.first;
+        th = it->second.second;
+    }
+}
+
+// Enqueue the passes of one frame; ctx->mu held.
+static dqj_status enqueue_frame(dqj_ctx *ctx, const dqj_params &p, const dqj_outputs &out, cudaStream_t st)
+{
+    int tw, th;
+    pick_tile(ctx, p, tw, th);
+    FrameDesc fd;
+    derive_frame(p, fd, tw, th);
+    fd.pitch = out.pitch_px;
+    fd.iter = out.iter;
+    fd.depth = out.depth;
+    fd.normal = out.normal;
+    fd.rgba = out.rgba;
+    const uint64_t px = (uint64_t)p.width * (uint64_t)p.height;
+    dqj_status s = scratch_ensure(ctx->scratch, px, p.precision == DQJ_FP32_RECHECK);
+    if (s != DQJ_OK) return s;
+    ScratchBuf &sb = ctx->scratch;
+    if (++sb.epoch == 0) {  // tags wrapped: clear the per-pixel flags
+        cudaError_t e = cudaMemsetAsync(sb.view.dirty_flag, 0, (size_t)sb.pixels * sizeof(uint32_t), st);
+        if (e != cudaSuccess) return cuda_fail(e, "render: clear flags");
+        sb.epoch = 1;
+    }
+    fd.epoch = sb.epoch;
+    cudaError_t e = cudaStreamWaitEvent(st, ctx->done_ev, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "render: cudaStreamWaitEvent");
+    e = cudaMemsetAsync(sb.view.ctr, 0, sizeof(Counters), st);
+    if (e != cudaSuccess) return cuda_fail(e, "render: clear counters");
+    cudaEvent_t *ev = nullptr;
+    if (ctx->ring_frames > 0) ev = &ctx->ev[5 * (ctx->ring_next++ % (uint64_t)ctx->ring_frames)];
+    e = launch_frame(fd, sb.view, st, ctx->num_sms, ev);
+    if (e != cudaSuccess) return cuda_fail(e, "render: kernel launch");
+    if (out.stats) {
+        e = cudaMemcpyAsync(out.stats, sb.view.ctr->stats, DQJ_NSTATS * sizeof(int64_t), cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e, "render: stats copy");
+    }
+    e = cudaEventRecord(ctx->done_ev, st);
+    if (e != cudaSuccess) return cuda_fail(e, "render: cudaEventRecord");
+    return DQJ_OK;
+}
+
+static dqj_status check_outputs(const dqj_params &p, const dqj_outputs *out)
+{
+    if (!out) return fail(DQJ_ERR_INVALID, "outputs is NULL");
+    if (out->pitch_px < p.width) return fail(DQJ_ERR_INVALID, "pitch_px must be >= width");
+    if (out->rgba && (reinterpret_cast<uintptr_t>(out->rgba) & 3u))
+        return fail(DQJ_ERR_INVALID, "rgba must be 4-byte aligned");
+    if (out->iter && (reinterpret_cast<uintptr_t>(out->iter) & 3u))
+        return fail(DQJ_ERR_INVALID, "iter must be 4-byte aligned");
+    if (out->depth && (reinterpret_cast<uintptr_t>(out->depth) & 3u))
+        return fail(DQJ_ERR_INVALID, "depth must be 4-byte aligned");
+    if (out->normal && (reinterpret_cast<uintptr_t>(out->normal) & 3u))
+        return fail(DQJ_ERR_INVALID, "normal must be 4-byte aligned");
+    return DQJ_OK;
+}
+
+dqj_status render_on_stream(dqj_ctx *ctx, const dqj_params *p, const dqj_outputs *out, cudaStream_t st)
+{
+    dqj_status s = validate(p);
+    if (s != DQJ_OK) return s;
+    s = check_outputs(*p, out);
+    if (s != DQJ_OK) return s;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(e, "render: cudaSetDevice");
+    return enqueue_frame(ctx, *p, *out, st);
+}
+
+}  // namespace dqj
+
+using namespace dqj;
+
+extern "C" {
+
+const char *dqj_last_error(void) { return g_err.c_str(); }
+
+dqj_status dqj_default_params(dqj_params *p)
+{
+    if (!p) return fail(DQJ_ERR_INVALID, "params is NULL");
+    std::memset(p, 0, sizeof *p);
+    const double c[8] = {-0.2, 0.6, 0.2, 0.2, 0.1, 0.0, 0.0, 0.05};
+    for (int i = 0; i < 8; ++i) p->c[i] = c[i];
+    for (int a = 0; a < 3; ++a) p->slice_basis[a][a] = 1.0;
+    p->eye[2] = 3.5;
+    p->up[1] = 1.0;
+    p->fov_y_deg = 45.0;
+    p->width = 256;
+    p->height = 256;
+    p->max_iter = 12;
+    p->escape_radius = 4.0;
+    p->march_steps = 256;
+    p->bisect_steps = 8;
+    p->normal_h = 1e-4;
+    for (int a = 0; a < 3; ++a) {
+        p->box_min[a] = -2.0;
+        p->box_max[a] = 2.0;
+        p->light_dir[a] = 1.0;
+        p->albedo[a] = 1.0;
+    }
+    p->k_ambient = 0.15;
+    p->k_diffuse = 0.85;
+    p->precision = DQJ_FP32;
+    p->recheck_margin = 1e-3;
+    p->square_mode = DQJ_SQUARE_ALGEBRAIC;
+    p->modulus_mode = DQJ_MODULUS_EUCLID8;
+    return DQJ_OK;
+}
+
+dqj_status dqj_validate_params(const dqj_params *p) { return validate(p); }
+
+dqj_status dqj_create(const dqj_config *cfg, dqj_ctx **out)
+{
+    if (!out) return fail(DQJ_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    dqj_config c{};
+    if (cfg) c = *cfg;
+    if (c.mem_budget_bytes == 0) c.mem_budget_bytes = 16ull << 30;
+    if (c.max_pending <= 0) c.max_pending = 4096;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) return cuda_fail(e, "create: cudaGetDeviceCount");
+    if (c.device < 0 || c.device >= ndev) return fail(DQJ_ERR_INVALID, "device ordinal out of range");
+    e = cudaSetDevice(c.device);
+    if (e != cudaSuccess) return cuda_fail(e, "create: cudaSetDevice");
+    dqj_ctx *ctx = new (std::nothrow) dqj_ctx();
+    if (!ctx) return fail(DQJ_ERR_NOMEM, "create: out of host memory");
+    ctx->device = c.device;
+    ctx->cfg = c;
+    if (c.autotune_cache) ctx->cache_path = c.autotune_cache;
+    ctx->cfg.autotune_cache = nullptr;
+    e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, c.device);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->done_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->host_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        dqj_status s = cuda_fail(e, "create");
+        if (ctx->done_ev) cudaEventDestroy(ctx->done_ev);
+        delete ctx;
+        return s;
+    }
+    *out = ctx;
+    return DQJ_OK;
+}
+
+dqj_status dqj_render(dqj_ctx *ctx, const dqj_params *p, const dqj_outputs *out, void *cuda_stream)
+{
+    if (!ctx) return fail(DQJ_ERR_INVALID, "ctx is NULL");
+    return render_on_stream(ctx, p, out, static_cast<cudaStream_t>(cuda_stream));
+}
+
+dqj_status dqj_render_host(dqj_ctx *ctx, const dqj_params *p, const dqj_outputs *host_out)
+{
+    if (!ctx) return fail(DQJ_ERR_INVALID, "ctx is NULL");
+    dqj_status s = validate(p);
+    if (s != DQJ_OK) return s;
+    s = check_outputs(*p, host_out);
+    if (s != DQJ_OK) return s;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(e, "render_host: cudaSetDevice");
+    const size_t px = (size_t)p->width * (size_t)p->height;
+    const size_t need = px * 24 + 256 + DQJ_NSTATS * sizeof(int64_t);
+    if (need > ctx->host_planes_bytes) {
+        e = cudaStreamSynchronize(ctx->host_stream);
+        if (e == cudaSuccess && ctx->host_planes) e = cudaFree(ctx->host_planes);
+        ctx->host_planes = nullptr;
+        ctx->host_planes_bytes = 0;
+        if (e == cudaSuccess) e = cudaMalloc(&ctx->host_planes, need);
+        if (e != cudaSuccess) return cuda_fail(e, "render_host: device planes");
+        ctx->host_planes_bytes = need;
+    }
+    char *b = static_cast<char *>(ctx->host_planes);
+    dqj_outputs dev{};
+    dev.pitch_px = p->width;
+    dev.iter = host_out->iter ? reinterpret_cast<int32_t *>(b) : nullptr;
+    dev.depth = host_out->depth ? reinterpret_cast<float *>(b + px * 4) : nullptr;
+    dev.normal = host_out->normal ? reinterpret_cast<float *>(b + px * 8) : nullptr;
+    dev.rgba = host_out->rgba ? reinterpret_cast<uint8_t *>(b + px * 20) : nullptr;
+    dev.stats = host_out->stats ? reinterpret_cast<int64_t *>(b + align_up(px * 24, 256)) : nullptr;
+    cudaStream_t st = ctx->host_stream;
+    s = enqueue_frame(ctx, *p, dev, st);
+    if (s != DQJ_OK) return s;
+    const size_t w = (size_t)p->width, hp = (size_t)host_out->pitch_px;
+    auto copy2d = [&](void *dst, const void *src, size_t elem) {
+        return cudaMemcpy2DAsync(dst, hp * elem, src, w * elem, w * elem, (size_t)p->height, cudaMemcpyDeviceToHost,
+                                 st);
+    };
+    if (e == cudaSuccess && host_out->iter) e = copy2d(host_out->iter, dev.iter, 4);
+    if (e == cudaSuccess && host_out->depth) e = copy2d(host_out->depth, dev.depth, 4);
+    if (e == cudaSuccess && host_out->normal) e = copy2d(host_out->normal, dev.normal, 12);
+    if (e == cudaSuccess && host_out->rgba) e = copy2d(host_out->rgba, dev.rgba, 4);
+    if (e == cudaSuccess && host_out->stats)
+        e = cudaMemcpyAsync(host_out->stats, dev.stats, DQJ_NSTATS * sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "render_host: copy back");
+    return DQJ_OK;
+}
+
+static void free_ring(dqj_ctx *ctx)
+{
+    for (auto &v : ctx->ev)
+        if (v) cudaEventDestroy(v);
+    ctx->ev.clear();
+    ctx->ring_frames = 0;
+    ctx->ring_next = 0;
+}
+
+dqj_status dqj_set_profiling(dqj_ctx *ctx, int32_t ring_frames)
+{
+    if (!ctx) return fail(DQJ_ERR_INVALID, "ctx is NULL");
+    if (ring_frames < 0 || ring_frames > 4096) return fail(DQJ_ERR_INVALID, "ring_frames must be in 0..4096");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e == cudaSuccess && ctx->done_ev) e = cudaEventSynchronize(ctx->done_ev);
+    if (e != cudaSuccess) return cuda_fail(e, "set_profiling");
+    free_ring(ctx);
+    if (ring_frames == 0) return DQJ_OK;
+    ctx->ev.assign((size_t)ring_frames * 5, nullptr);
+    for (auto &v : ctx->ev) {
+        e = cudaEventCreate(&v);
+        if (e != cudaSuccess) {
+            free_ring(ctx);
+            return cuda_fail(e, "set_profiling: cudaEventCreate");
+        }
+    }
+    ctx->ring_frames = ring_frames;
+    return DQJ_OK;
+}
+
+dqj_status dqj_pass_ms(dqj_ctx *ctx, int32_t frames, float *ms)
+{
+    if (!ctx || !ms) return fail(DQJ_ERR_INVALID, "ctx or ms is NULL");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (frames < 1 || frames > ctx->ring_frames) return fail(DQJ_ERR_INVALID, "frames must be in 1..ring_frames");
+    if ((uint64_t)frames > ctx->ring_next) return fail(DQJ_ERR_NOT_FOUND, "fewer renders were recorded");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    for (int f = 0; f < frames && e == cudaSuccess; ++f) {
+        const uint64_t idx = ctx->ring_next - (uint64_t)frames + (uint64_t)f;
+        cudaEvent_t *ev = &ctx->ev[5 * (idx % (uint64_t)ctx->ring_frames)];
+        e = cudaEventSynchronize(ev[4]);
+        for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventElapsedTime(&ms[4 * f + i], ev[i], ev[i + 1]);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "pass_ms");
+    return DQJ_OK;
+}
+
+dqj_status dqj_fma_peak(int32_t device, int32_t variant, int32_t launches, double *flops_per_s)
+{
+    if (!flops_per_s) return fail(DQJ_ERR_INVALID, "flops_per_s is NULL");
+    if (variant < 0 || variant > 4) return fail(DQJ_ERR_INVALID, "variant must be in 0..4");
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) return cuda_fail(e, "fma_peak: cudaSetDevice");
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) return cuda_fail(e, "fma_peak: attribute");
+    float *sink = nullptr;
+    e = cudaMalloc(&sink, (size_t)sms * 2048 * sizeof(float));
+    if (e != cudaSuccess) return cuda_fail(e, "fma_peak: cudaMalloc");
+    double best = 0.0;
+    for (int i = 0; i < (launches > 0 ? launches : 1) && e == cudaSuccess; ++i) {
+        double f = 0.0;
+        e = fma_peak_launch(variant, sms, sink, nullptr, &f);
+        if (f > best) best = f;
+    }
+    cudaFree(sink);
+    if (e != cudaSuccess) return cuda_fail(e, "fma_peak: launch");
+    *flops_per_s = best;
+    return DQJ_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,63 @@
+// runtime.h -- host-side context of libdqj (internal).
+#pragma once
+
+#include <atomic>
+#include <condition_variable>
+#include <cstdint>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/dqj.h"
+#include "dqj_internal.h"
+
+namespace dqj {
+
+// Thread-local error message behind dqj_last_error().
+dqj_status fail(dqj_status st, const std::string &msg);
+dqj_status cuda_fail(cudaError_t e, const char *what);
+
+// Validation and derivation of the per-frame constants (host, double).
+dqj_status validate(const dqj_params *p);
+void derive_frame(const dqj_params &p, FrameDesc &fd, int tile_w, int tile_h);
+
+// Scratch block sized for a pixel count; grow-only.
+struct ScratchBuf {
+    void *base = nullptr;
+    size_t bytes = 0;
+    uint32_t pixels = 0;
+    bool with_queue = false;
+    Scratch view{};
+    uint32_t epoch = 0;
+};
+dqj_status scratch_ensure(ScratchBuf &s, uint64_t pixels, bool need_queue);
+void scratch_free(ScratchBuf &s);
+
+struct ServeState;  // serving loop, serve.cpp
+
+}  // namespace dqj
+
+struct dqj_ctx {
+    int device = 0;
+    int num_sms = 0;
+    dqj_config cfg{};
+    std::string cache_path;
+    std::mutex mu;                   // orders renders on this context
+    dqj::ScratchBuf scratch;
+    cudaEvent_t done_ev = nullptr;   // last render's completion on its stream
+    // dqj_render_host planes
+    cudaStream_t host_stream = nullptr;
+    void *host_planes = nullptr;
+    size_t host_planes_bytes = 0;
+    int64_t *host_stats_dev = nullptr;
+    // tile shapes chosen by the autotuner, keyed by (pixel-count class, iter bucket)
+    std::map<int, std::pair<int, int>> tiles;
+    dqj::ServeState *serve = nullptr;
+    // profiling ring: ring_frames x 5 events, next slot, renders recorded
+    std::vector<cudaEvent_t> ev;
+    int ring_frames = 0;
+    uint64_t ring_next = 0;
+};

@@ -79,7 +79,7 @@ def default_scene(**overrides) -> dict:
         "k_ambient": 0.15,
         "k_diffuse": 0.85,
         "albedo": [1.0, 1.0, 1.0],
-        "precision": PRECISION_FP32_RECHECK,
+        "precision": PRECISION_FP32,
         "recheck_margin": 1e-3,
         "square_mode": SQUARE_ALGEBRAIC,
         "modulus_mode": MODULUS_EUCLID8,

@@ -1,0 +1,66 @@
+"""CPU checks of the C ABI: the library loads, exports every function that
+include/dqj.h declares, its defaults match the single-frame scene, and host-side
+validation rejects bad parameter blocks with a message (no GPU needed)."""
+import numpy as np
+import pytest
+
+from paper_2303_14827_gb300 import binding, scenes
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return binding.load()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = binding.declared_symbols()
+    assert {"dqj_create", "dqj_render", "dqj_submit", "dqj_poll", "dqj_destroy", "dqj_last_error"} <= set(names)
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_default_params_match_single_frame_scene(lib):
+    p = binding.dqj_default_params()
+    d = binding.params_to_dict(p)
+    want = scenes.default_scene()
+    for k, v in want.items():
+        assert np.allclose(np.asarray(d[k], dtype=float), np.asarray(v, dtype=float), rtol=0, atol=0), k
+    assert binding.dqj_validate_params(p) == binding.DQJ_OK
+
+
+BAD = [
+    ("width", 0), ("width", 16385), ("height", -1), ("max_iter", 0), ("max_iter", 1025),
+    ("escape_radius", 0.0), ("escape_radius", float("nan")), ("march_steps", 0), ("march_steps", 65536),
+    ("bisect_steps", -1), ("bisect_steps", 31), ("fov_y_deg", 0.0), ("fov_y_deg", 180.0), ("normal_h", 0.0),
+    ("precision", 3), ("recheck_margin", -0.1), ("square_mode", 2), ("modulus_mode", -1),
+    ("box_min", [2.0, -2.0, -2.0]), ("light_dir", [0.0, 0.0, 0.0]), ("albedo", [1.5, 1.0, 1.0]),
+    ("target", [0.0, 0.0, 3.5]), ("up", [0.0, 0.0, 1.0]), ("c", [float("inf")] + [0.0] * 7),
+]
+
+
+@pytest.mark.parametrize("field,value", BAD)
+def test_validation_rejects(lib, field, value):
+    s = scenes.default_scene(**{field: value})
+    assert binding.dqj_validate_params(s) == binding.DQJ_ERR_INVALID
+    assert binding.last_error()
+
+
+def test_validation_rejects_non_orthonormal_basis(lib):
+    b = [[1, 0, 0, 0, 0, 0, 0, 0], [0, 1, 0, 0, 0, 0, 0, 0], [0, 1e-6, 1, 0, 0, 0, 0, 0]]
+    assert binding.dqj_validate_params(scenes.default_scene(slice_basis=b)) == binding.DQJ_ERR_INVALID
+    assert "orthonormal" in binding.last_error()
+
+
+def test_validation_accepts_config_scenes(lib):
+    assert binding.dqj_validate_params(scenes.default_scene()) == binding.DQJ_OK
+    assert binding.dqj_validate_params(scenes.full_hd_scene(0)) == binding.DQJ_OK
+    for s in scenes.batch_scenes(1, 8):
+        assert binding.dqj_validate_params(s) == binding.DQJ_OK
+
+
+def test_null_arguments_are_errors_not_crashes(lib):
+    assert lib.dqj_validate_params(None) == binding.DQJ_ERR_INVALID
+    assert lib.dqj_create(None, None) == binding.DQJ_ERR_INVALID
+    assert lib.dqj_destroy(None) == binding.DQJ_ERR_INVALID
+    assert lib.dqj_render(None, None, None, None) == binding.DQJ_ERR_INVALID
+    assert binding.last_error()

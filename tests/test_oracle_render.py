@@ -245,3 +245,32 @@ def test_pixel_list_equals_full_image():
     assert np.array_equal(part["iter"], full["iter"].reshape(-1)[pix])
     assert np.array_equal(part["depth"], full["depth"].reshape(-1)[pix])
     assert np.array_equal(part["rgba"], full["rgba"].reshape(-1, 4)[pix])
+
+
+def test_normal_overflow_guard_c0():
+    # At c = 0 the field is F(q) = |q|^(2^(n*+1)) in closed form.  Where any of the
+    # six neighbours has F > 2^100 the normal is -d; elsewhere it is the
+    # normalised central difference.  h = 0.01 gives both cases in one image.
+    W = H = 40
+    s = scenes.default_scene(c=[0.0] * 8, width=W, height=H, fov_y_deg=60.0, normal_h=0.01)
+    out = oracle.render(s)
+    e = 2.0 ** (s["max_iter"] + 1)
+    n_guard = n_grad = 0
+    for j in range(H):
+        for i in range(W):
+            depth = out["depth"][j, i]
+            if not np.isfinite(depth):
+                continue
+            o, d = oracle.camera_ray(s, i, j)
+            p = o + depth * d
+            logs = [e * math.log(np.linalg.norm(p + sg * s["normal_h"] * ax)) for ax in np.eye(3) for sg in (1, -1)]
+            nrm = out["normal"][j, i]
+            if max(logs) > 100 * math.log(2.0):
+                assert np.allclose(nrm, -d, atol=0), (i, j)
+                n_guard += 1
+            else:
+                F = np.exp(logs)
+                g = np.array([F[0] - F[1], F[2] - F[3], F[4] - F[5]])
+                assert float(np.dot(nrm, g / np.linalg.norm(g))) > 1.0 - 1e-9
+                n_grad += 1
+    assert n_guard > 10 and n_grad > 10, (n_guard, n_grad)
