@@ -1,19 +1,26 @@
-// dq_math.cuh -- dual-quaternion Julia step, escape modulus and lockstep
-// classification on the device, templated on float / double.
+// dq_math.cuh -- dual-quaternion Julia step with its escape test, templated on
+// float / double, plus a paired FP32 form that advances two samples per thread.
 //
 // A dual quaternion zeta = q_r + q_d eps is kept in 8 registers (q_r | q_d),
 // scalar first in each half (appendix, quaternion and dual-quaternion
 // definitions).  The square is expanded in closed form instead of the general
 // product:
 //   ALGEBRAIC (eps^2 = 0, appendix product):
-//     q_r^2           = (r0^2 - r1^2 - r2^2 - r3^2, 2 r0 r1, 2 r0 r2, 2 r0 r3)
-//                       (Eq. quatsq)
+//     q_r^2             = (r0^2 - r1^2 - r2^2 - r3^2, 2 r0 r1, 2 r0 r2, 2 r0 r3)
+//                         (Eq. quatsq)
 //     q_r q_d + q_d q_r = 2 (r0 d0 - v_r . v_d, r0 v_d + d0 v_r)
-//                       (the cross products cancel)
+//                         (the cross products cancel)
 //   PAPER_COMPONENTWISE (the equation printed beside Eq. dqjulia2):
 //     q_r^2 + q_d^2 eps, each half by Eq. quatsq.
 // The escape test compares the modulus with R^2 (Method, "Practical
 // Considerations"); EUCLID8 takes |q_r|^2 + |q_d|^2, DUALNUM |q_r|^2.
+//
+// One step computes zeta_{n+1} = zeta_n^2 + c and m = modulus(zeta_{n+1}).  The
+// partial sum sp = r1^2 + r2^2 + r3^2 of the escape test of step n is carried
+// into step n+1, whose real scalar r0^2 - r1^2 - r2^2 - r3^2 + c0 is
+// r0^2 + (c0 - sp): the three squares are formed once, not twice.  (Offsetting
+// sp by -R^2 would save nothing and cost accuracy: c0 - R^2 and sp - R^2 are
+// both near -R^2, and their difference loses bits when the iterate is small.)
 #pragma once
 
 #include "dqj_internal.h"
@@ -23,49 +30,59 @@ namespace dqj {
 __device__ __forceinline__ float dfma(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double dfma(double a, double b, double c) { return fma(a, b, c); }
 
-// zeta <- zeta^2 + c
-template <typename T, int SQ>
-__device__ __forceinline__ void dq_step(T (&z)[8], const T (&c)[8])
+// sp of zeta: r1^2 + r2^2 + r3^2
+template <typename T>
+__device__ __forceinline__ T dq_sp(const T (&z)[8])
 {
-    const T r0 = z[0], r1 = z[1], r2 = z[2], r3 = z[3];
-    const T d0 = z[4], d1 = z[5], d2 = z[6], d3 = z[7];
+    return dfma(z[3], z[3], dfma(z[2], z[2], z[1] * z[1]));
+}
+
+// zo = zi^2 + c; returns modulus(zo) and updates sp.  zo and zi may be the
+// same array; loops that alternate two arrays avoid copying the state back.
+template <typename T, int SQ, int MOD>
+__device__ __forceinline__ T dq_iter(const T (&zi)[8], T (&z)[8], T &sp, const T (&c)[8])
+{
+    const T r0 = zi[0], r1 = zi[1], r2 = zi[2], r3 = zi[3];
+    const T d0 = zi[4], d1 = zi[5], d2 = zi[6], d3 = zi[7];
     const T tr0 = r0 + r0;
-    T nr0 = dfma(r0, r0, c[0]);
-    nr0 = dfma(-r1, r1, nr0);
-    nr0 = dfma(-r2, r2, nr0);
-    nr0 = dfma(-r3, r3, nr0);
-    z[0] = nr0;
+    z[0] = dfma(r0, r0, dfma(sp, T(-1), c[0]));
     z[1] = dfma(tr0, r1, c[1]);
     z[2] = dfma(tr0, r2, c[2]);
     z[3] = dfma(tr0, r3, c[3]);
+    const T td0 = d0 + d0;
     if (SQ == 0) {
-        const T td0 = d0 + d0;
-        T p = r0 * d0;
-        p = dfma(-r1, d1, p);
-        p = dfma(-r2, d2, p);
-        p = dfma(-r3, d3, p);
-        z[4] = dfma(T(2), p, c[4]);
+        T q = r1 * d1;
+        q = dfma(r2, d2, q);
+        q = dfma(r3, d3, q);
+        z[4] = dfma(q, T(-2), dfma(tr0, d0, c[4]));
         z[5] = dfma(tr0, d1, dfma(td0, r1, c[5]));
         z[6] = dfma(tr0, d2, dfma(td0, r2, c[6]));
         z[7] = dfma(tr0, d3, dfma(td0, r3, c[7]));
     } else {
-        const T td0 = d0 + d0;
-        T nd0 = dfma(d0, d0, c[4]);
-        nd0 = dfma(-d1, d1, nd0);
-        nd0 = dfma(-d2, d2, nd0);
-        nd0 = dfma(-d3, d3, nd0);
-        z[4] = nd0;
+        T q = d1 * d1;
+        q = dfma(d2, d2, q);
+        q = dfma(d3, d3, q);
+        z[4] = dfma(q, T(-1), dfma(d0, d0, c[4]));
         z[5] = dfma(td0, d1, c[5]);
         z[6] = dfma(td0, d2, c[6]);
         z[7] = dfma(td0, d3, c[7]);
     }
+    sp = dq_sp<T>(z);
+    T x = dfma(z[0], z[0], sp);
+    if (MOD == 0) {
+        x = dfma(z[4], z[4], x);
+        x = dfma(z[5], z[5], x);
+        x = dfma(z[6], z[6], x);
+        x = dfma(z[7], z[7], x);
+    }
+    return x;
 }
 
-// modulus(zeta) - R^2, with R^2 folded into the first term
+// modulus(zeta), the scalar field of the normal estimate
 template <typename T, int MOD>
-__device__ __forceinline__ T modulus_minus(const T (&z)[8], T R2)
+__device__ __forceinline__ T modulus(const T (&z)[8])
 {
-    T x = dfma(z[0], z[0], -R2);
+    T x = z[0] * z[0];
     x = dfma(z[1], z[1], x);
     x = dfma(z[2], z[2], x);
     x = dfma(z[3], z[3], x);
@@ -78,19 +95,13 @@ __device__ __forceinline__ T modulus_minus(const T (&z)[8], T R2)
     return x;
 }
 
-template <typename T, int MOD>
-__device__ __forceinline__ T modulus(const T (&z)[8])
-{
-    return modulus_minus<T, MOD>(z, T(0));
-}
-
 // Escape-time classification of one sample per lane, all 32 lanes in step.
 // Every lane runs the same straight-line iteration each trip; a lane that has
 // escaped keeps iterating (its result is no longer used) so that no lane ever
 // diverges.  The trip loop ends when no lane in the warp is still bounded, or at
 // max_iter.  `part` = the lane has a sample.  Returns the escape count in
 // 1..max_iter, or 0 when the sample stayed bounded for max_iter steps.  With
-// RECHECK, *marginal reports whether any tested modulus lay within F.margin of
+// RECHECK, `marginal` reports whether any tested modulus lay within F.margin of
 // R^2 (up to and including the escaping step).
 template <typename T, int SQ, int MOD, bool RECHECK>
 __device__ __forceinline__ int classify_lockstep(T (&z)[8], const FrameT<T> &F, int max_iter, bool part,
@@ -99,11 +110,18 @@ __device__ __forceinline__ int classify_lockstep(T (&z)[8], const FrameT<T> &F, 
     bool alive = part;
     bool mg = false;
     int cnt = 0;
-    for (int n = 0; n < max_iter; ++n) {
-        dq_step<T, SQ>(z, F.c);
-        const T x = modulus_minus<T, MOD>(z, F.R2);
-        if (RECHECK) mg = mg || (alive && fabs(x) <= F.margin);
-        alive = alive && (x <= T(0));
+    T sp = dq_sp<T>(z);
+    T w[8];
+    // two steps per trip, z -> w -> z, with the escape test after each
+    for (int n = 0; n < max_iter; n += 2) {
+        T m = dq_iter<T, SQ, MOD>(z, w, sp, F.c);
+        if (RECHECK) mg = mg || (alive && fabs(m - F.R2) <= F.margin);
+        alive = alive && (m <= F.R2);
+        cnt += alive ? 1 : 0;
+        if (!__any_sync(0xffffffffu, alive) || n + 1 >= max_iter) break;
+        m = dq_iter<T, SQ, MOD>(w, z, sp, F.c);
+        if (RECHECK) mg = mg || (alive && fabs(m - F.R2) <= F.margin);
+        alive = alive && (m <= F.R2);
         cnt += alive ? 1 : 0;
         if (!__any_sync(0xffffffffu, alive)) break;
     }
@@ -116,11 +134,106 @@ __device__ __forceinline__ int classify_lockstep(T (&z)[8], const FrameT<T> &F, 
 template <typename T, int SQ, int MOD>
 __device__ __forceinline__ int classify_scalar(T (&z)[8], const FrameT<T> &F, int max_iter)
 {
-    for (int n = 1; n <= max_iter; ++n) {
-        dq_step<T, SQ>(z, F.c);
-        if (modulus_minus<T, MOD>(z, F.R2) > T(0)) return n;
-    }
+    T sp = dq_sp<T>(z);
+    for (int n = 1; n <= max_iter; ++n)
+        if (dq_iter<T, SQ, MOD>(z, z, sp, F.c) > F.R2) return n;
     return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Paired form: two independent samples per thread, one in each half of a
+// float2, advanced together by the sm_100+ paired FP32 instructions
+// (fma.rn.f32x2, add.rn.f32x2, mul.rn.f32x2).  Per half the arithmetic is
+// exactly dq_iter<float>, so both forms round identically.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+
+__device__ __forceinline__ float2 dq_sp2(const float2 (&z)[8])
+{
+    return f2fma(z[3], z[3], f2fma(z[2], z[2], f2mul(z[1], z[1])));
+}
+
+template <int SQ, int MOD>
+__device__ __forceinline__ float2 dq_iter2(const float2 (&zi)[8], float2 (&z)[8], float2 &sp, const PairConsts &P)
+{
+    const float2 r0 = zi[0], r1 = zi[1], r2 = zi[2], r3 = zi[3];
+    const float2 d0 = zi[4], d1 = zi[5], d2 = zi[6], d3 = zi[7];
+    const float2 tr0 = f2add(r0, r0);
+    z[0] = f2fma(r0, r0, f2fma(sp, P.neg1, P.c[0]));
+    z[1] = f2fma(tr0, r1, P.c[1]);
+    z[2] = f2fma(tr0, r2, P.c[2]);
+    z[3] = f2fma(tr0, r3, P.c[3]);
+    const float2 td0 = f2add(d0, d0);
+    if (SQ == 0) {
+        float2 q = f2mul(r1, d1);
+        q = f2fma(r2, d2, q);
+        q = f2fma(r3, d3, q);
+        z[4] = f2fma(q, P.neg2, f2fma(tr0, d0, P.c[4]));
+        z[5] = f2fma(tr0, d1, f2fma(td0, r1, P.c[5]));
+        z[6] = f2fma(tr0, d2, f2fma(td0, r2, P.c[6]));
+        z[7] = f2fma(tr0, d3, f2fma(td0, r3, P.c[7]));
+    } else {
+        float2 q = f2mul(d1, d1);
+        q = f2fma(d2, d2, q);
+        q = f2fma(d3, d3, q);
+        z[4] = f2fma(q, P.neg1, f2fma(d0, d0, P.c[4]));
+        z[5] = f2fma(td0, d1, P.c[5]);
+        z[6] = f2fma(td0, d2, P.c[6]);
+        z[7] = f2fma(td0, d3, P.c[7]);
+    }
+    sp = dq_sp2(z);
+    float2 x = f2fma(z[0], z[0], sp);
+    if (MOD == 0) {
+        x = f2fma(z[4], z[4], x);
+        x = f2fma(z[5], z[5], x);
+        x = f2fma(z[6], z[6], x);
+        x = f2fma(z[7], z[7], x);
+    }
+    return x;
+}
+
+// Lockstep classification of two samples per lane (halves .x and .y), same
+// conventions as classify_lockstep.  On entry aa / ab say whether each half has
+// a sample; on return they say whether it stayed bounded (inside), and ca / cb
+// hold the number of steps it stayed bounded (escape count - 1, or max_iter).
+template <int SQ, int MOD, bool RECHECK>
+__device__ __forceinline__ void classify_lockstep2(float2 (&z)[8], const PairConsts &P, float R2, float margin,
+                                                   int max_iter, bool &aa, bool &ab, int &ca, int &cb, bool &mga,
+                                                   bool &mgb)
+{
+    bool ma = false, mb = false;
+    int na = 0, nb = 0;
+    float2 sp = dq_sp2(z);
+    float2 w[8];
+    // two steps per trip, z -> w -> z, with the escape test after each
+    for (int n = 0; n < max_iter; n += 2) {
+        float2 x = dq_iter2<SQ, MOD>(z, w, sp, P);
+        if (RECHECK) {
+            ma = ma || (aa && fabsf(x.x - R2) <= margin);
+            mb = mb || (ab && fabsf(x.y - R2) <= margin);
+        }
+        aa = aa && (x.x <= R2);
+        ab = ab && (x.y <= R2);
+        na += aa ? 1 : 0;
+        nb += ab ? 1 : 0;
+        if (!__any_sync(0xffffffffu, aa || ab) || n + 1 >= max_iter) break;
+        x = dq_iter2<SQ, MOD>(w, z, sp, P);
+        if (RECHECK) {
+            ma = ma || (aa && fabsf(x.x - R2) <= margin);
+            mb = mb || (ab && fabsf(x.y - R2) <= margin);
+        }
+        aa = aa && (x.x <= R2);
+        ab = ab && (x.y <= R2);
+        na += aa ? 1 : 0;
+        nb += ab ? 1 : 0;
+        if (!__any_sync(0xffffffffu, aa || ab)) break;
+    }
+    ca = na;
+    cb = nb;
+    mga = ma;
+    mgb = mb;
 }
 
 }  // namespace dqj

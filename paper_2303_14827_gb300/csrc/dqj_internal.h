@@ -37,11 +37,20 @@ struct FrameT {
 //                       bit i of path = 1 when level i moved lo up to mid
 constexpr int kMarchSample = 31;
 
+// Broadcast pairs (v, v) for the paired FP32 march kernel (see dq_math.cuh).
+struct PairConsts {
+    float2 c[8];
+    float2 A[8];
+    float2 neg1, neg2;
+};
+
 struct FrameDesc {
     FrameT<float> f;
     FrameT<double> d;
+    PairConsts p2;
     int32_t W, H, max_iter, N, B;
     int32_t square_mode, modulus_mode, precision;
+    int32_t march_variant;   // FP32 march: 0 one ray per lane, 1 two rays per lane (paired FP32)
     int32_t tile_w, tile_h, tiles_x, tiles_y;
     int64_t pitch;
     int32_t *iter;

@@ -282,6 +282,108 @@ __global__ void __launch_bounds__(kBlock) march_kernel(const __grid_constant__ F
 }
 
 // ---------------------------------------------------------------------------
+// march, paired: two rays per lane, tile slots `lane` and `lane + 32` of a
+// 64-ray tile, advanced together in the two halves of float2 registers by the
+// paired FP32 instructions.  Same per-ray arithmetic as march_kernel<float>.
+// Per ray it keeps only running sums: sum_* (steps stayed bounded, summed over
+// samples), max_* (largest escape count - 1), prev_* (escape count - 1 of the
+// latest outside sample) and the first inside sample kf_*; the iteration and
+// sample counts follow from them once the ray is done.
+// ---------------------------------------------------------------------------
+template <int SQ, int MOD, bool RECHECK>
+__global__ void __launch_bounds__(kBlock, 5) march2_kernel(const __grid_constant__ FrameDesc fd, const Scratch sc)
+{
+    const FrameT<float> &F = fd.f;
+    const PairConsts &P = fd.p2;
+    const int lane = threadIdx.x & 31;
+    const unsigned ntiles = (unsigned)fd.tiles_x * (unsigned)fd.tiles_y;
+    const int N = fd.N, max_iter = fd.max_iter;
+    unsigned long long s_iters = 0, s_samples = 0, s_hits = 0, s_rechecks = 0;
+    for (;;) {
+        unsigned tile = 0;
+        if (lane == 0) tile = atomicAdd(&sc.ctr->tile_next, 1u);
+        tile = __shfl_sync(kFull, tile, 0);
+        if (tile >= ntiles) break;
+        const int tx = (int)(tile % (unsigned)fd.tiles_x), ty = (int)(tile / (unsigned)fd.tiles_x);
+        const int sb = lane + 32;
+        const int xa = tx * fd.tile_w + lane % fd.tile_w, ya = ty * fd.tile_h + lane / fd.tile_w;
+        const int xb = tx * fd.tile_w + sb % fd.tile_w, yb = ty * fd.tile_h + sb / fd.tile_w;
+        const bool va = xa < fd.W && ya < fd.H, vb = xb < fd.W && yb < fd.H;
+        float da[3] = {0.f, 0.f, 1.f}, db[3] = {0.f, 0.f, 1.f};
+        float tia = 0.f, toa = 0.f, tib = 0.f, tob = 0.f;
+        const bool boxa = va && camera_clip<float>(F, fd.W, fd.H, xa, ya, da, tia, toa);
+        const bool boxb = vb && camera_clip<float>(F, fd.W, fd.H, xb, yb, db, tib, tob);
+        if (!boxa) tia = toa = 0.f;
+        if (!boxb) tib = tob = 0.f;
+        float2 D[8];
+        {
+            float Da[8], Db[8];
+            slice_dir<float>(F, da, Da);
+            slice_dir<float>(F, db, Db);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) D[i] = make_float2(Da[i], Db[i]);
+        }
+        const float2 tin = make_float2(tia, tib);
+        const float2 dl = make_float2((toa - tia) / (float)N, (tob - tib) / (float)N);
+        bool acta = boxa, actb = boxb;
+        int suma = 0, sumb = 0, maxa = 0, maxb = 0, preva = 0, prevb = 0, kfa = -1, kfb = -1;
+        float2 kf = make_float2(0.f, 0.f);
+        for (int k = 0; k <= N; ++k) {
+            if (!__any_sync(kFull, acta || actb)) break;
+            const float2 t = f2fma(kf, dl, tin);
+            kf = f2add(kf, make_float2(1.f, 1.f));
+            float2 z[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) z[i] = f2fma(t, D[i], P.A[i]);
+            bool ina = acta, inb = actb, mga, mgb;
+            int ca, cb;
+            classify_lockstep2<SQ, MOD, RECHECK>(z, P, F.R2, F.margin, max_iter, ina, inb, ca, cb, mga, mgb);
+            if (RECHECK) {
+                const bool pa = acta && mga, pb = actb && mgb;
+                if (warp_push(pa, make_int4(ya * fd.W + xa, k | (kMarchSample << 16), 0, ina ? 0 : ca + 1), sc.queue,
+                              sc.queue_cap, &sc.ctr->queue_count)) {
+                    atomicAdd(&sc.ctr->stats[7], 1ull);
+                    mark_dirty(fd, sc, ya * fd.W + xa);
+                }
+                if (warp_push(pb, make_int4(yb * fd.W + xb, k | (kMarchSample << 16), 0, inb ? 0 : cb + 1), sc.queue,
+                              sc.queue_cap, &sc.ctr->queue_count)) {
+                    atomicAdd(&sc.ctr->stats[7], 1ull);
+                    mark_dirty(fd, sc, yb * fd.W + xb);
+                }
+                s_rechecks += (pa ? 1 : 0) + (pb ? 1 : 0);
+            }
+            // ina / inb imply acta / actb (they start equal and only clear)
+            suma += ca;
+            sumb += cb;
+            maxa = max(maxa, ca);
+            maxb = max(maxb, cb);
+            if (acta && !ina) preva = ca;
+            if (actb && !inb) prevb = cb;
+            if (ina) kfa = k;
+            if (inb) kfb = k;
+            acta = acta && !ina;
+            actb = actb && !inb;
+        }
+        const bool hita = kfa >= 0, hitb = kfb >= 0;
+        // iterations = sum of (escape count) over escaped samples + max_iter per inside sample
+        //            = sum of bounded steps + number of escaped samples
+        const int nesca = hita ? kfa : N + 1, nescb = hitb ? kfb : N + 1;
+        s_iters += (boxa ? suma + nesca : 0) + (boxb ? sumb + nescb : 0);
+        s_samples += (boxa ? nesca + (hita ? 1 : 0) : 0) + (boxb ? nescb + (hitb ? 1 : 0) : 0);
+        s_hits += (hita ? 1 : 0) + (hitb ? 1 : 0);
+        if (va && !hita) write_miss<float>(fd, xa, ya, boxa ? maxa + 1 : 0);
+        if (vb && !hitb) write_miss<float>(fd, xb, yb, boxb ? maxb + 1 : 0);
+        warp_push(hita, make_int4(ya * fd.W + xa, kfa, preva + 1, 0), sc.hits, sc.hit_cap, &sc.ctr->hit_count);
+        warp_push(hitb, make_int4(yb * fd.W + xb, kfb, prevb + 1, 0), sc.hits, sc.hit_cap, &sc.ctr->hit_count);
+    }
+    flush_stat(&sc.ctr->stats[0], s_iters);
+    flush_stat(&sc.ctr->stats[8], s_iters);
+    flush_stat(&sc.ctr->stats[2], s_samples);
+    flush_stat(&sc.ctr->stats[3], s_hits);
+    if (RECHECK) flush_stat(&sc.ctr->stats[4], s_rechecks);
+}
+
+// ---------------------------------------------------------------------------
 // bisect + normal + shade over the hit list
 // ---------------------------------------------------------------------------
 template <typename T, int SQ, int MOD, bool RECHECK>
@@ -360,8 +462,9 @@ __global__ void __launch_bounds__(kBlock) bisect_kernel(const __grid_constant__ 
                 T z[8];
 #pragma unroll
                 for (int i = 0; i < 8; ++i) z[i] = dfma(hs, F.E[a][i], dfma(depth, D[i], F.A[i]));
+                T sp = dq_sp<T>(z);
                 for (int n = 0; n < nmax; ++n)
-                    if (n < n_star) dq_step<T, SQ>(z, F.c);
+                    if (n < n_star) dq_iter<T, SQ, MOD>(z, z, sp, F.c);
                 fv[s] = modulus<T, MOD>(z);
                 guard = guard || !(fv[s] <= normal_fmax(T(0)));
             }
@@ -488,7 +591,8 @@ __global__ void __launch_bounds__(kBlock) fixup_kernel(const __grid_constant__ F
                 p[a] += s == 0 ? F.h : -F.h;
                 double z[8];
                 for (int j = 0; j < 8; ++j) z[j] = F.O[j] + p[0] * F.E[0][j] + p[1] * F.E[1][j] + p[2] * F.E[2][j];
-                for (int n = 0; n < n_star; ++n) dq_step<double, SQ>(z, F.c);
+                double sp = dq_sp<double>(z);
+                for (int n = 0; n < n_star; ++n) dq_iter<double, SQ, MOD>(z, z, sp, F.c);
                 its += n_star;
                 fv[s] = modulus<double, MOD>(z);
                 guard = guard || !(fv[s] <= normal_fmax(0.0));
@@ -516,14 +620,23 @@ int persistent_grid(K kernel, int num_sms)
 template <typename T, int SQ, int MOD, bool RECHECK>
 cudaError_t launch_passes(const FrameDesc &fd, const Scratch &sc, cudaStream_t st, int num_sms, cudaEvent_t *ev)
 {
-    static int g_march = 0, g_bisect = 0;
-    if (!g_march) g_march = persistent_grid(march_kernel<T, SQ, MOD, RECHECK>, num_sms);
-    if (!g_bisect) g_bisect = persistent_grid(bisect_kernel<T, SQ, MOD, RECHECK>, num_sms);
+    static int g_march = 0, g_march2 = 0, g_bisect = 0;
     const unsigned ntiles = (unsigned)fd.tiles_x * (unsigned)fd.tiles_y;
-    const int gm = (int)min((unsigned)g_march, (ntiles + 3u) / 4u);
     if (ev) cudaEventRecord(ev[0], st);
-    march_kernel<T, SQ, MOD, RECHECK><<<gm > 0 ? gm : 1, kBlock, 0, st>>>(fd, sc);
+    if constexpr (sizeof(T) == 4) {
+        if (fd.march_variant == 1) {
+            if (!g_march2) g_march2 = persistent_grid(march2_kernel<SQ, MOD, RECHECK>, num_sms);
+            const int gm = (int)min((unsigned)g_march2, (ntiles + 3u) / 4u);
+            march2_kernel<SQ, MOD, RECHECK><<<gm > 0 ? gm : 1, kBlock, 0, st>>>(fd, sc);
+        }
+    }
+    if (sizeof(T) != 4 || fd.march_variant != 1) {
+        if (!g_march) g_march = persistent_grid(march_kernel<T, SQ, MOD, RECHECK>, num_sms);
+        const int gm = (int)min((unsigned)g_march, (ntiles + 3u) / 4u);
+        march_kernel<T, SQ, MOD, RECHECK><<<gm > 0 ? gm : 1, kBlock, 0, st>>>(fd, sc);
+    }
     if (ev) cudaEventRecord(ev[1], st);
+    if (!g_bisect) g_bisect = persistent_grid(bisect_kernel<T, SQ, MOD, RECHECK>, num_sms);
     const unsigned maxw = ((unsigned)fd.W * (unsigned)fd.H + 31u) / 32u;
     const int gb = (int)min((unsigned)g_bisect, (maxw + 3u) / 4u);
     bisect_kernel<T, SQ, MOD, RECHECK><<<gb > 0 ? gb : 1, kBlock, 0, st>>>(fd, sc);

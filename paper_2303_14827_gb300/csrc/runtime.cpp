@@ -4,6 +4,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -139,6 +140,12 @@ void derive_frame(const dqj_params &p, FrameDesc &fd, int tile_w, int tile_h)
     F.ka = p.k_ambient;
     F.kd = p.k_diffuse;
     cast_frame<float>(F, fd.f);
+    for (int i = 0; i < 8; ++i) {
+        fd.p2.c[i] = make_float2(fd.f.c[i], fd.f.c[i]);
+        fd.p2.A[i] = make_float2(fd.f.A[i], fd.f.A[i]);
+    }
+    fd.p2.neg1 = make_float2(-1.f, -1.f);
+    fd.p2.neg2 = make_float2(-2.f, -2.f);
     fd.W = p.width;
     fd.H = p.height;
     fd.max_iter = p.max_iter;
@@ -207,28 +214,40 @@ dqj_status scratch_ensure(ScratchBuf &s, uint64_t pixels, bool need_queue)
     return DQJ_OK;
 }
 
-// Tile shape of a frame: the autotuned one for its class, else 8 x 4.
-static void pick_tile(dqj_ctx *ctx, const dqj_params &p, int &tw, int &th)
+// March kernel and tile shape of a frame: the autotuned choice for its class,
+// else the paired kernel on 8 x 8 tiles (FP32) or one ray per lane on 8 x 4
+// (FP64).  The environment variable DQJ_MARCH_VARIANT (0 or 1) overrides the
+// FP32 kernel: 0 one ray per lane, 1 two rays per lane.
+static void pick_tile(dqj_ctx *ctx, const dqj_params &p, int &variant, int &tw, int &th)
 {
+    variant = p.precision == DQJ_FP64 ? 0 : 1;
+    if (const char *e = std::getenv("DQJ_MARCH_VARIANT"))
+        if (e[0] == '0' || e[0] == '1') variant = p.precision == DQJ_FP64 ? 0 : e[0] - '0';
     tw = 8;
-    th = 4;
+    th = variant >= 1 ? 8 : 4;
     const int64_t px = (int64_t)p.width * p.height;
     const int cls = px <= 65536 ? 0 : px <= 262144 ? 1 : px <= 1048576 ? 2 : 3;
-    const int key = cls * 4 + (p.max_iter <= 12 ? 0 : p.max_iter <= 20 ? 1 : p.max_iter <= 28 ? 2 : 3);
+    const int key = (variant * 4 + cls) * 4 + (p.max_iter <= 12 ? 0 : p.max_iter <= 20 ? 1 : p.max_iter <= 28 ? 2 : 3);
     auto it = ctx->tiles.find(key);
     if (it != ctx->tiles.end()) {
         tw = it->second.first;
         th = it->second.second;
+    }
+    // a warp covers 32 rays (one per lane) or 64 (two per lane)
+    if (tw < 1 || th < 1 || tw * th != (variant >= 1 ? 64 : 32)) {
+        tw = 8;
+        th = variant >= 1 ? 8 : 4;
     }
 }
 
 // Enqueue the passes of one frame; ctx->mu held.
 static dqj_status enqueue_frame(dqj_ctx *ctx, const dqj_params &p, const dqj_outputs &out, cudaStream_t st)
 {
-    int tw, th;
-    pick_tile(ctx, p, tw, th);
+    int variant, tw, th;
+    pick_tile(ctx, p, variant, tw, th);
     FrameDesc fd;
     derive_frame(p, fd, tw, th);
+    fd.march_variant = variant;
     fd.pitch = out.pitch_px;
     fd.iter = out.iter;
     fd.depth = out.depth;

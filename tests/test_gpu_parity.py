@@ -163,3 +163,26 @@ def test_full_hd_precision_modes_sampled(rdr, precision):
     o = oracle.render(s, pixels=pix)
     sub = {k: g[k].reshape((-1,) + g[k].shape[2:])[pix] for k in ("iter", "depth", "normal", "rgba")}
     assert_parity(compare(sub, o), what=f"1080p precision {precision}")
+
+
+@pytest.mark.parametrize("scene", ["single", "hd3", "batch2", "paper"])
+def test_march_variants_bitwise_equal(rdr, scene, monkeypatch):
+    # The two FP32 march kernels (one ray per lane; two rays per lane in float2
+    # halves) run the same per-sample arithmetic in the same order, so their
+    # images must be identical.
+    if scene == "single":
+        s = scenes.default_scene(width=200, height=150)
+    elif scene == "hd3":
+        s = scenes.full_hd_scene(3)
+    elif scene == "batch2":
+        s = scenes.batch_scenes(seed=1, n=3)[2]
+    else:
+        s = scenes.default_scene(c=list(scenes.PAPER_C_VALUES["highres"]), width=161, height=97, max_iter=15)
+    outs = []
+    for v in ("0", "1"):
+        monkeypatch.setenv("DQJ_MARCH_VARIANT", v)
+        outs.append(gpu_render(rdr, s))
+    for o in outs[1:]:
+        for k in ("iter", "depth", "normal", "rgba"):
+            assert np.array_equal(o[k], outs[0][k]), k
+        assert o["stats"] == outs[0]["stats"]
