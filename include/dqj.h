@@ -197,6 +197,34 @@ dqj_status dqj_destroy(dqj_ctx *ctx);
 dqj_status dqj_set_profiling(dqj_ctx *ctx, int32_t ring_frames);
 dqj_status dqj_pass_ms(dqj_ctx *ctx, int32_t frames, float *ms);
 
+/* Largest width * height dqj_render_noalloc accepts (e.g. 512 x 512). */
+#define DQJ_NOALLOC_MAX_PIXELS 262144u
+
+/*
+ * dqj_render_noalloc -- the plain render without any device allocation.  (An
+ * interface of this library; the paper has no counterpart.)
+ *
+ * For callers that must not allocate device memory.  Examples: a host
+ * application that reserves all device memory for its own pool before loading
+ * this library, or a frame loop that must not block on the allocator.
+ * It needs no context: its scratch (the counter block and hit list of the march
+ * and bisection passes) is a fixed array inside the library, about 4 MiB, which
+ * every device that loads the library holds until the process exits.
+ *
+ * p, out and cuda_stream as for dqj_render: out holds caller-owned DEVICE planes
+ * (and an optional device stats array).  Runs on the current device; the first
+ * call on each device looks up the array's device address with
+ * cudaGetSymbolAddress, so make that first call before any stream capture.
+ * Stream-ordered: enqueues and returns.  Allocates nothing (no cudaMalloc,
+ * cudaFree or allocating library routine).  Errors: DQJ_ERR_INVALID when
+ * width * height > DQJ_NOALLOC_MAX_PIXELS or precision is DQJ_FP32_RECHECK
+ * (only DQJ_FP32 and DQJ_FP64 are supported), plus dqj_render's checks.
+ * Every call shares the one array and clears its counters at the start; calls
+ * that overlap on the GPU (different streams or threads) race on it, so order
+ * them on one stream.
+ */
+dqj_status dqj_render_noalloc(const dqj_params *p, const dqj_outputs *out, void *cuda_stream);
+
 /* Message for the last non-OK status on this thread ("" if none). */
 const char *dqj_last_error(void);
 

@@ -121,6 +121,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         L.dqj_last_error.restype = ctypes.c_char_p
         L.dqj_last_error.argtypes = []
         L.dqj_fma_peak.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P(ctypes.c_double)]
+        L.dqj_render_noalloc.argtypes = [P(dqj_params), P(dqj_outputs), ctypes.c_void_p]
         L.dqj_set_profiling.argtypes = [ctypes.c_void_p, ctypes.c_int32]
         L.dqj_pass_ms.argtypes = [ctypes.c_void_p, ctypes.c_int32, P(ctypes.c_float)]
         for name in declared_symbols():
@@ -218,6 +219,17 @@ def dqj_render(ctx: int, scene: dict, outputs: dqj_outputs, stream: int = 0) -> 
 def dqj_render_host(ctx: int, scene: dict, outputs: dqj_outputs) -> None:
     p = make_params(scene)
     check(load().dqj_render_host(ctypes.c_void_p(ctx), ctypes.byref(p), ctypes.byref(outputs)))
+
+
+DQJ_NOALLOC_MAX_PIXELS = 262144
+
+
+def dqj_render_noalloc(scene: dict, outputs: dqj_outputs, stream: int = 0) -> None:
+    """Render on the current device without any device allocation: the scratch
+    is a fixed array inside the library (for callers that must not allocate
+    device memory).  At most DQJ_NOALLOC_MAX_PIXELS pixels; FP32 or FP64."""
+    p = make_params(scene)
+    check(load().dqj_render_noalloc(ctypes.byref(p), ctypes.byref(outputs), ctypes.c_void_p(stream)))
 
 
 def dqj_submit(ctx: int, scene: dict, outputs: dqj_outputs) -> int:
