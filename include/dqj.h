@@ -68,9 +68,16 @@ enum {
     DQJ_MODULUS_DUALNUM = 1  /* |q_r|^2, the dual-number modulus of zeta zeta*      */
 };
 
+/* dqj_config.device value for a CPU-only context whose serving entry points run
+ * against a mock device (for testing admission, budgets and timeouts without a
+ * GPU); it cannot render.  The mock reads DQJ_MOCK_DELAY_US (run time of a
+ * request, default 1000) and DQJ_MOCK_FAIL ("nomem": every admission fails,
+ * "hang": no request ever completes) from the environment at dqj_create. */
+#define DQJ_DEVICE_MOCK (-1)
+
 /* Per-context configuration for dqj_create. */
 typedef struct {
-    int32_t device;            /* CUDA device ordinal                                   */
+    int32_t device;            /* CUDA device ordinal, or DQJ_DEVICE_MOCK               */
     uint64_t mem_budget_bytes; /* serving: device bytes admitted requests may occupy
                                   (outputs the library allocates + scratch); 0 = 16 GiB */
     int32_t max_pending;       /* serving: host queue bound; 0 = 4096                   */
@@ -183,7 +190,11 @@ dqj_status dqj_submit(dqj_ctx *ctx, const dqj_params *p, const dqj_outputs *out,
  * once finished; the ticket is then consumed (a second poll: DQJ_ERR_NOT_FOUND). */
 dqj_status dqj_poll(dqj_ctx *ctx, dqj_ticket ticket, int *done, dqj_status *result);
 
-/* Cancel queued requests, wait (bounded) for admitted ones, free everything. */
+/* Cancel queued requests (their tickets finish with DQJ_ERR_CANCELLED), wait for
+ * admitted ones for at most DQJ_DESTROY_TIMEOUT_MS (environment, default 10000)
+ * and free everything.  DQJ_ERR_TIMEOUT when admitted requests were still
+ * running; their device memory is then left allocated rather than freed under a
+ * kernel that may still use it. */
 dqj_status dqj_destroy(dqj_ctx *ctx);
 
 /* Profiling: with ring_frames > 0 (at most 4096), every later render on this

@@ -44,7 +44,7 @@ struct PairConsts {
     float2 neg1, neg2;
 };
 
-struct FrameDesc {
+struct alignas(16) FrameDesc {
     FrameT<float> f;
     FrameT<double> d;
     PairConsts p2;
@@ -57,6 +57,7 @@ struct FrameDesc {
     float *depth;
     float *normal;
     uint8_t *rgba;
+    int64_t *stats;   // served requests: caller's DQJ_NSTATS counters (device), or NULL
     uint32_t epoch;   // tag for per-pixel dirty flags, changes every frame
     uint32_t pad;
 };
@@ -76,7 +77,7 @@ struct Counters {
 static_assert(sizeof(Counters) == 128, "Counters layout");
 
 // Views into one scratch allocation owned by a context.
-struct Scratch {
+struct alignas(16) Scratch {
     Counters *ctr;
     int4 *hits;           // {pixel, k_first, n_prev, 0}
     uint32_t hit_cap;

@@ -1,0 +1,381 @@
+// render_common.cuh -- device helpers shared by the render kernels and the
+// persistent serving kernel: camera ray and box clip, slice map, warp-aggregated
+// queue pushes, output writes and shading, and the per-tile bodies of the march
+// and bisection passes.
+#pragma once
+
+#include "dq_math.cuh"
+
+namespace dqj {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kBlock = 128;  // 4 warps per CTA
+
+// Per-lane counters, added to the frame's stats once per warp (DQJ_STAT_*).
+struct LaneStats {
+    unsigned long long iters = 0, samples = 0, hits = 0, rechecks = 0, niters = 0;
+};
+
+
+template <typename T>
+__device__ __forceinline__ const FrameT<T> &frame(const FrameDesc &fd);
+template <>
+__device__ __forceinline__ const FrameT<float> &frame<float>(const FrameDesc &fd) { return fd.f; }
+template <>
+__device__ __forceinline__ const FrameT<double> &frame<double>(const FrameDesc &fd) { return fd.d; }
+
+template <typename T>
+__device__ __forceinline__ T tinf();
+template <>
+__device__ __forceinline__ float tinf<float>() { return __int_as_float(0x7f800000); }
+template <>
+__device__ __forceinline__ double tinf<double>() { return __longlong_as_double(0x7ff0000000000000ll); }
+
+// Pinhole camera ray through pixel centre (x + 0.5, y + 0.5), row 0 at the top,
+// and its slab clip against the box, t >= 0.  Returns false when the ray misses
+// the box (t_in >= t_out).  The FP64 form follows the reference formula term by
+// term; the FP32 form folds the pixel-to-screen map into one FMA per axis.
+template <typename T>
+__device__ __forceinline__ bool camera_clip(const FrameT<T> &F, int W, int H, int x, int y, T (&d)[3], T &t_in,
+                                            T &t_out)
+{
+    T sx, sy;
+    if constexpr (sizeof(T) == 4) {
+        sx = dfma(T(x) + T(0.5), F.sxa, F.sxb);
+        sy = dfma(T(y) + T(0.5), F.sya, F.syb);
+    } else {
+        sx = (T(2) * (T(x) + T(0.5)) / T(W) - T(1)) * F.th * F.aspect;
+        sy = (T(1) - T(2) * (T(y) + T(0.5)) / T(H)) * F.th;
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) d[a] = F.fwd[a] + sx * F.right[a] + sy * F.upv[a];
+    const T len = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) d[a] = d[a] / len;
+    T t0 = -tinf<T>(), t1 = tinf<T>();
+    bool ok = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (d[a] == T(0)) {
+            if (F.eye[a] < F.bmin[a] || F.eye[a] > F.bmax[a]) ok = false;
+        } else {
+            T ta = (F.bmin[a] - F.eye[a]) / d[a];
+            T tb = (F.bmax[a] - F.eye[a]) / d[a];
+            if (ta > tb) {
+                const T tmp = ta;
+                ta = tb;
+                tb = tmp;
+            }
+            t0 = ta > t0 ? ta : t0;
+            t1 = tb < t1 ? tb : t1;
+        }
+    }
+    if (t0 < T(0)) t0 = T(0);
+    t_in = t0;
+    t_out = t1;
+    return ok && (t0 < t1);
+}
+
+// D = E d: direction of the ray in the 8-D slice.
+template <typename T>
+__device__ __forceinline__ void slice_dir(const FrameT<T> &F, const T (&d)[3], T (&D)[8])
+{
+#pragma unroll
+    for (int i = 0; i < 8; ++i) D[i] = dfma(d[0], F.E[0][i], dfma(d[1], F.E[1][i], d[2] * F.E[2][i]));
+}
+
+// Warp-aggregated append of one int4 per flagged lane.  All lanes must call.
+// Returns true on the lanes whose entry did not fit (the caller falls back).
+__device__ __forceinline__ bool warp_push(bool flag, int4 v, int4 *buf, unsigned cap, unsigned *count)
+{
+    const unsigned m = __ballot_sync(kFull, flag);
+    if (m == 0) return false;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(m) - 1;
+    unsigned base = 0;
+    if (lane == leader) base = atomicAdd(count, (unsigned)__popc(m));
+    base = __shfl_sync(kFull, base, leader);
+    if (!flag) return false;
+    const unsigned slot = base + __popc(m & ((1u << lane) - 1u));
+    if (slot < cap) {
+        buf[slot] = v;
+        return false;
+    }
+    return true;
+}
+
+// Queue a pixel for an FP64 re-render once per frame.
+__device__ __forceinline__ void mark_dirty(const FrameDesc &fd, const Scratch &sc, int pixel)
+{
+    const uint32_t old = atomicExch(&sc.dirty_flag[pixel], fd.epoch);
+    if (old != fd.epoch) {
+        const unsigned slot = atomicAdd(&sc.ctr->dirty_count, 1u);
+        if (slot < sc.dirty_cap) sc.dirty_list[slot] = pixel;
+    }
+}
+
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+__device__ __forceinline__ void flush_stat(unsigned long long *dst, unsigned long long v)
+{
+    v = warp_sum(v);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(dst, v);
+}
+
+template <typename T>
+__device__ __forceinline__ void write_miss(const FrameDesc &fd, int x, int y, int iter)
+{
+    const int64_t o = (int64_t)y * fd.pitch + x;
+    if (fd.iter) fd.iter[o] = iter;
+    if (fd.depth) fd.depth[o] = tinf<float>();
+    if (fd.normal) {
+        fd.normal[3 * o + 0] = 0.f;
+        fd.normal[3 * o + 1] = 0.f;
+        fd.normal[3 * o + 2] = 0.f;
+    }
+    if (fd.rgba) *reinterpret_cast<uchar4 *>(fd.rgba + 4 * o) = make_uchar4(0, 0, 0, 0);
+}
+
+__device__ __forceinline__ unsigned char to_u8(double v)
+{
+    double x = floor(255.0 * v + 0.5);
+    x = x < 0.0 ? 0.0 : (x > 255.0 ? 255.0 : x);
+    return (unsigned char)x;
+}
+__device__ __forceinline__ unsigned char to_u8(float v)
+{
+    float x = floorf(255.f * v + 0.5f);
+    x = x < 0.f ? 0.f : (x > 255.f ? 255.f : x);
+    return (unsigned char)x;
+}
+
+// Largest normal-field value used for a gradient, 2^100 (exact in float and
+// double): larger or non-finite field values select the fallback normal -d.
+__device__ __forceinline__ float normal_fmax(float) { return 1.2676506002282294e30f; }
+__device__ __forceinline__ double normal_fmax(double) { return 1.2676506002282294e30; }
+
+// Normalise the central-difference gradient (fallback -d when guard is set or
+// the gradient vanishes), shade with the ambient and diffuse terms of Eq. phong
+// and write a hit pixel.  The gradient is scaled by its largest component first
+// so that its squared length cannot overflow.
+template <typename T>
+__device__ __forceinline__ void shade_write(const FrameDesc &fd, const FrameT<T> &F, int x, int y, int iter,
+                                            T depth, const T (&g)[3], bool guard, const T (&d)[3])
+{
+    T n[3];
+    const T s = fmax(fabs(g[0]), fmax(fabs(g[1]), fabs(g[2])));
+    if (guard || !(s > T(0))) {
+        n[0] = -d[0];
+        n[1] = -d[1];
+        n[2] = -d[2];
+    } else {
+        const T g0 = g[0] / s, g1 = g[1] / s, g2 = g[2] / s;
+        const T gl = sqrt(g0 * g0 + g1 * g1 + g2 * g2);
+        n[0] = g0 / gl;
+        n[1] = g1 / gl;
+        n[2] = g2 / gl;
+    }
+    T ndl = n[0] * F.light[0] + n[1] * F.light[1] + n[2] * F.light[2];
+    ndl = ndl > T(0) ? ndl : T(0);
+    T v = F.ka + F.kd * ndl;
+    v = v < T(0) ? T(0) : (v > T(1) ? T(1) : v);
+    const int64_t o = (int64_t)y * fd.pitch + x;
+    if (fd.iter) fd.iter[o] = iter;
+    if (fd.depth) fd.depth[o] = (float)depth;
+    if (fd.normal) {
+        fd.normal[3 * o + 0] = (float)n[0];
+        fd.normal[3 * o + 1] = (float)n[1];
+        fd.normal[3 * o + 2] = (float)n[2];
+    }
+    if (fd.rgba)
+        *reinterpret_cast<uchar4 *>(fd.rgba + 4 * o) =
+            make_uchar4(to_u8(v * F.albedo[0]), to_u8(v * F.albedo[1]), to_u8(v * F.albedo[2]), 255);
+}
+
+// One 64-ray tile of the paired march (see march2_kernel); all 32 lanes call.
+template <int SQ, int MOD, bool RECHECK>
+__device__ __forceinline__ void march2_tile(const FrameDesc &fd, const PairConsts &P, const Scratch &sc, unsigned tile,
+                                            LaneStats &st)
+{
+    const FrameT<float> &F = fd.f;
+    const int lane = threadIdx.x & 31;
+    const int N = fd.N, max_iter = fd.max_iter;
+    const int tx = (int)(tile % (unsigned)fd.tiles_x), ty = (int)(tile / (unsigned)fd.tiles_x);
+    const int sb = lane + 32;
+    const int xa = tx * fd.tile_w + lane % fd.tile_w, ya = ty * fd.tile_h + lane / fd.tile_w;
+    const int xb = tx * fd.tile_w + sb % fd.tile_w, yb = ty * fd.tile_h + sb / fd.tile_w;
+    const bool va = xa < fd.W && ya < fd.H, vb = xb < fd.W && yb < fd.H;
+    float da[3] = {0.f, 0.f, 1.f}, db[3] = {0.f, 0.f, 1.f};
+    float tia = 0.f, toa = 0.f, tib = 0.f, tob = 0.f;
+    const bool boxa = va && camera_clip<float>(F, fd.W, fd.H, xa, ya, da, tia, toa);
+    const bool boxb = vb && camera_clip<float>(F, fd.W, fd.H, xb, yb, db, tib, tob);
+    if (!boxa) tia = toa = 0.f;
+    if (!boxb) tib = tob = 0.f;
+    float2 D[8];
+    {
+        float Da[8], Db[8];
+        slice_dir<float>(F, da, Da);
+        slice_dir<float>(F, db, Db);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) D[i] = make_float2(Da[i], Db[i]);
+    }
+    const float2 tin = make_float2(tia, tib);
+    const float2 dl = make_float2((toa - tia) / (float)N, (tob - tib) / (float)N);
+    bool acta = boxa, actb = boxb;
+    int suma = 0, sumb = 0, maxa = 0, maxb = 0, preva = 0, prevb = 0, kfa = -1, kfb = -1;
+    float2 kf = make_float2(0.f, 0.f);
+    for (int k = 0; k <= N; ++k) {
+        if (!__any_sync(kFull, acta || actb)) break;
+        const float2 t = f2fma(kf, dl, tin);
+        kf = f2add(kf, make_float2(1.f, 1.f));
+        float2 z[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) z[i] = f2fma(t, D[i], P.A[i]);
+        bool ina = acta, inb = actb, mga, mgb;
+        int ca, cb;
+        classify_lockstep2<SQ, MOD, RECHECK>(z, P, F.R2, F.margin, max_iter, ina, inb, ca, cb, mga, mgb);
+        if (RECHECK) {
+            const bool pa = acta && mga, pb = actb && mgb;
+            if (warp_push(pa, make_int4(ya * fd.W + xa, k | (kMarchSample << 16), 0, ina ? 0 : ca + 1), sc.queue,
+                          sc.queue_cap, &sc.ctr->queue_count)) {
+                atomicAdd(&sc.ctr->stats[7], 1ull);
+                mark_dirty(fd, sc, ya * fd.W + xa);
+            }
+            if (warp_push(pb, make_int4(yb * fd.W + xb, k | (kMarchSample << 16), 0, inb ? 0 : cb + 1), sc.queue,
+                          sc.queue_cap, &sc.ctr->queue_count)) {
+                atomicAdd(&sc.ctr->stats[7], 1ull);
+                mark_dirty(fd, sc, yb * fd.W + xb);
+            }
+            st.rechecks += (pa ? 1 : 0) + (pb ? 1 : 0);
+        }
+        // ina / inb imply acta / actb (they start equal and only clear)
+        suma += ca;
+        sumb += cb;
+        maxa = max(maxa, ca);
+        maxb = max(maxb, cb);
+        if (acta && !ina) preva = ca;
+        if (actb && !inb) prevb = cb;
+        if (ina) kfa = k;
+        if (inb) kfb = k;
+        acta = acta && !ina;
+        actb = actb && !inb;
+    }
+    const bool hita = kfa >= 0, hitb = kfb >= 0;
+    // iterations = sum of (escape count) over escaped samples + max_iter per inside sample
+    //            = sum of bounded steps + number of escaped samples
+    const int nesca = hita ? kfa : N + 1, nescb = hitb ? kfb : N + 1;
+    st.iters += (boxa ? suma + nesca : 0) + (boxb ? sumb + nescb : 0);
+    st.samples += (boxa ? nesca + (hita ? 1 : 0) : 0) + (boxb ? nescb + (hitb ? 1 : 0) : 0);
+    st.hits += (hita ? 1 : 0) + (hitb ? 1 : 0);
+    if (va && !hita) write_miss<float>(fd, xa, ya, boxa ? maxa + 1 : 0);
+    if (vb && !hitb) write_miss<float>(fd, xb, yb, boxb ? maxb + 1 : 0);
+    warp_push(hita, make_int4(ya * fd.W + xa, kfa, preva + 1, 0), sc.hits, sc.hit_cap, &sc.ctr->hit_count);
+    warp_push(hitb, make_int4(yb * fd.W + xb, kfb, prevb + 1, 0), sc.hits, sc.hit_cap, &sc.ctr->hit_count);
+}
+
+// Bisection, normal and shading of hit-list entries [base, base + 32) clipped to
+// nhits, one per lane (see bisect_kernel); all 32 lanes call.
+template <typename T, int SQ, int MOD, bool RECHECK>
+__device__ __forceinline__ void bisect_chunk(const FrameDesc &fd, const Scratch &sc, unsigned base, unsigned nhits,
+                                             LaneStats &st)
+{
+    const FrameT<T> &F = frame<T>(fd);
+    const int lane = threadIdx.x & 31;
+    const unsigned idx = base + lane;
+    const bool part = idx < nhits;
+    int4 e = make_int4(0, 0, 0, 0);
+    if (part) e = sc.hits[idx];
+    const int pixel = e.x, k_first = e.y;
+    const int x = pixel % fd.W, y = pixel / fd.W;
+    T d[3] = {T(0), T(0), T(1)};
+    T t_in = T(0), t_out = T(0);
+    if (part) camera_clip<T>(F, fd.W, fd.H, x, y, d, t_in, t_out);
+    T D[8];
+    slice_dir<T>(F, d, D);
+    const T delta = (t_out - t_in) / T(fd.N);
+    bool bis = part && k_first > 0;
+    T lo = bis ? dfma(T(k_first - 1), delta, t_in) : t_in;
+    T hi = bis ? dfma(T(k_first), delta, t_in) : t_in;
+    int n_lo = bis ? e.z : fd.max_iter;
+    unsigned path = 0;
+    unsigned iters = 0, samples = 0;
+    for (int b = 0; b < fd.B; ++b) {
+        const T mid = lo + T(0.5) * (hi - lo);
+        T z[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) z[i] = dfma(mid, D[i], F.A[i]);
+        bool mg;
+        const int n = classify_lockstep<T, SQ, MOD, RECHECK>(z, F, fd.max_iter, bis, mg);
+        if (RECHECK) {
+            const bool push = bis && mg;
+            if (warp_push(push, make_int4(pixel, k_first | (b << 16), (int)path, n), sc.queue, sc.queue_cap,
+                          &sc.ctr->queue_count)) {
+                atomicAdd(&sc.ctr->stats[7], 1ull);
+                mark_dirty(fd, sc, pixel);
+            }
+            st.rechecks += push ? 1 : 0;
+        }
+        if (bis) {
+            iters += n ? (unsigned)n : (unsigned)fd.max_iter;
+            samples += 1;
+            if (n == 0) {
+                hi = mid;
+            } else {
+                lo = mid;
+                n_lo = n;
+                path |= 1u << b;
+            }
+        }
+    }
+    const T depth = bis ? lo + T(0.5) * (hi - lo) : t_in;
+    const int n_star = n_lo;
+    // Normal: F(p) = modulus(zeta_{n*}(p)) at p +- h e_a, iterated n* times.
+    // zeta0 = A + depth D +- h E_a (the slice image of eye + depth d +- h e_a).
+    int nmax = part ? n_star : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nmax = max(nmax, __shfl_xor_sync(kFull, nmax, o));
+    T g[3];
+    bool guard = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        T fv[2];
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            const T hs = s == 0 ? F.h : -F.h;
+            T z[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) z[i] = dfma(hs, F.E[a][i], dfma(depth, D[i], F.A[i]));
+            T sp = dq_sp<T>(z);
+            for (int n = 0; n < nmax; ++n)
+                if (n < n_star) dq_iter<T, SQ, MOD>(z, z, sp, F.c);
+            fv[s] = modulus<T, MOD>(z);
+            guard = guard || !(fv[s] <= normal_fmax(T(0)));
+        }
+        g[a] = fv[0] - fv[1];
+    }
+    if (part) {
+        st.niters += 6ull * (unsigned)n_star;
+        shade_write<T>(fd, F, x, y, n_star, depth, g, guard, d);
+    }
+    st.iters += iters;
+    st.samples += samples;
+}
+
+// Add a warp's lane counters to the frame's stats.
+template <bool RECHECK>
+__device__ __forceinline__ void flush_lane_stats(const Scratch &sc, const LaneStats &st, bool march)
+{
+    flush_stat(&sc.ctr->stats[0], st.iters);
+    if (march) flush_stat(&sc.ctr->stats[8], st.iters);
+    flush_stat(&sc.ctr->stats[1], st.niters);
+    flush_stat(&sc.ctr->stats[2], st.samples);
+    flush_stat(&sc.ctr->stats[3], st.hits);
+    if (RECHECK) flush_stat(&sc.ctr->stats[4], st.rechecks);
+}
+
+}  // namespace dqj

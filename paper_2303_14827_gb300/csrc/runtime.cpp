@@ -218,7 +218,7 @@ dqj_status scratch_ensure(ScratchBuf &s, uint64_t pixels, bool need_queue)
 // else the paired kernel on 8 x 8 tiles (FP32) or one ray per lane on 8 x 4
 // (FP64).  The environment variable DQJ_MARCH_VARIANT (0 or 1) overrides the
 // FP32 kernel: 0 one ray per lane, 1 two rays per lane.
-static void pick_tile(dqj_ctx *ctx, const dqj_params &p, int &variant, int &tw, int &th)
+void pick_tile_shape(dqj_ctx *ctx, const dqj_params &p, int &variant, int &tw, int &th)
 {
     variant = p.precision == DQJ_FP64 ? 0 : 1;
     if (const char *e = std::getenv("DQJ_MARCH_VARIANT"))
@@ -244,7 +244,7 @@ static void pick_tile(dqj_ctx *ctx, const dqj_params &p, int &variant, int &tw, 
 static dqj_status enqueue_frame(dqj_ctx *ctx, const dqj_params &p, const dqj_outputs &out, cudaStream_t st)
 {
     int variant, tw, th;
-    pick_tile(ctx, p, variant, tw, th);
+    pick_tile_shape(ctx, p, variant, tw, th);
     FrameDesc fd;
     derive_frame(p, fd, tw, th);
     fd.march_variant = variant;
@@ -301,6 +301,7 @@ dqj_status render_on_stream(dqj_ctx *ctx, const dqj_params *p, const dqj_outputs
     if (s != DQJ_OK) return s;
     s = check_outputs(*p, out);
     if (s != DQJ_OK) return s;
+    if (ctx->device == DQJ_DEVICE_MOCK) return fail(DQJ_ERR_INVALID, "a mock context cannot render");
     std::lock_guard<std::mutex> lk(ctx->mu);
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_fail(e, "render: cudaSetDevice");
@@ -357,6 +358,15 @@ dqj_status dqj_create(const dqj_config *cfg, dqj_ctx **out)
     if (cfg) c = *cfg;
     if (c.mem_budget_bytes == 0) c.mem_budget_bytes = 16ull << 30;
     if (c.max_pending <= 0) c.max_pending = 4096;
+    if (c.device == DQJ_DEVICE_MOCK) {
+        dqj_ctx *ctx = new (std::nothrow) dqj_ctx();
+        if (!ctx) return fail(DQJ_ERR_NOMEM, "create: out of host memory");
+        ctx->device = DQJ_DEVICE_MOCK;
+        ctx->cfg = c;
+        ctx->cfg.autotune_cache = nullptr;
+        *out = ctx;
+        return DQJ_OK;
+    }
     int ndev = 0;
     cudaError_t e = cudaGetDeviceCount(&ndev);
     if (e != cudaSuccess) return cuda_fail(e, "create: cudaGetDeviceCount");
@@ -391,6 +401,7 @@ dqj_status dqj_render(dqj_ctx *ctx, const dqj_params *p, const dqj_outputs *out,
 dqj_status dqj_render_host(dqj_ctx *ctx, const dqj_params *p, const dqj_outputs *host_out)
 {
     if (!ctx) return fail(DQJ_ERR_INVALID, "ctx is NULL");
+    if (ctx->device == DQJ_DEVICE_MOCK) return fail(DQJ_ERR_INVALID, "a mock context cannot render");
     dqj_status s = validate(p);
     if (s != DQJ_OK) return s;
     s = check_outputs(*p, host_out);

@@ -38,6 +38,8 @@ void scratch_free(ScratchBuf &s);
 
 struct ServeState;  // serving loop, serve.cpp
 
+dqj_status serve_start(dqj_ctx *ctx);
+
 }  // namespace dqj
 
 struct dqj_ctx {
@@ -61,3 +63,8 @@ struct dqj_ctx {
     int ring_frames = 0;
     uint64_t ring_next = 0;
 };
+
+namespace dqj {
+// March kernel variant and tile shape for a frame (autotuned choice or default).
+void pick_tile_shape(dqj_ctx *ctx, const dqj_params &p, int &variant, int &tw, int &th);
+}  // namespace dqj
