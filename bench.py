@@ -339,6 +339,10 @@ def run_gpu(args, world, rank, local):
                        "d2h_bytes_per_step": nf * (W * H * 24 + 8 * binding.DQJ_NSTATS),
                        "frames_per_s": nf * args.steps * world / dt}
 
+    if not args.no_serve:
+        line["served"] = serving_section(local)
+        line["batch64"] = batch_section(local)
+
     if rank == 0 and not args.no_cpu_baseline:
         rate, _, cores, desc, _ = oracle_sample_rate(args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
@@ -348,6 +352,191 @@ def run_gpu(args, world, rank, local):
         print(json.dumps(line), flush=True)
     return 0
 
+
+
+# ---------------------------------------------------------------------------
+# served form: saturation, Poisson latency, and the mixed 64-frame batch
+# ---------------------------------------------------------------------------
+class OutputPool:
+    """Reusable device output planes per resolution (caller-owned outputs must
+    stay valid until the request completes).  Planes are allocated up front by
+    prefill: a device synchronize after an allocation would wait for the
+    persistent serving launch, so `misses` counts allocations made later."""
+
+    def __init__(self, device):
+        self.device = device
+        self.free = {}
+        self.misses = 0
+
+    def _alloc(self, w, h):
+        from paper_2303_14827_gb300 import binding
+        return binding.alloc_outputs(w, h, device=self.device)
+
+    def prefill(self, reqs):
+        import collections
+
+        import torch
+        need = collections.Counter((s["width"], s["height"]) for s in reqs)
+        for key, n in need.items():
+            lst = self.free.setdefault(key, [])
+            while len(lst) < n:
+                lst.append(self._alloc(*key))
+        torch.cuda.synchronize(self.device)  # the library writes outputs from its own streams
+
+    def get(self, w, h):
+        import torch
+        lst = self.free.setdefault((w, h), [])
+        if lst:
+            return lst.pop()
+        self.misses += 1
+        o = self._alloc(w, h)
+        torch.cuda.synchronize(self.device)
+        return o
+
+    def put(self, w, h, o):
+        self.free.setdefault((w, h), []).append(o)
+
+
+def served_run(ctx, reqs, arrivals, pool):
+    """Submit reqs[i] at time arrivals[i] (seconds from start, sorted), poll until
+    all are done.  Returns (latencies in s, makespan s)."""
+    from paper_2303_14827_gb300 import binding
+    n = len(reqs)
+    lat = [None] * n
+    inflight = {}
+    nxt = 0
+    t0 = time.perf_counter()
+    last_done = t0
+    while nxt < n or inflight:
+        now = time.perf_counter() - t0
+        while nxt < n and arrivals[nxt] <= now:
+            s = reqs[nxt]
+            o = pool.get(s["width"], s["height"])
+            try:
+                t = binding.dqj_submit(ctx, s, binding.outputs_of(o))
+            except binding.DqjError as e:
+                if e.status != binding.DQJ_ERR_BUSY:
+                    raise
+                pool.put(s["width"], s["height"], o)
+                break
+            inflight[t] = (nxt, o, t0 + arrivals[nxt])
+            nxt += 1
+        for t in list(inflight):
+            done, st = binding.dqj_poll(ctx, t)
+            if done:
+                i, o, ta = inflight.pop(t)
+                assert st == binding.DQJ_OK, st
+                tn = time.perf_counter()
+                lat[i] = tn - ta
+                last_done = tn
+                s = reqs[i]
+                pool.put(s["width"], s["height"], o)
+    return lat, last_done - t0
+
+
+def plain_back_to_back(ctx, reqs, pool, stream):
+    """The same requests rendered one after another with dqj_render on one stream."""
+    import torch
+
+    from paper_2303_14827_gb300 import binding
+    outs = [pool.get(s["width"], s["height"]) for s in reqs]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s, o in zip(reqs, outs):
+        binding.dqj_render(ctx, s, binding.outputs_of(o), stream.cuda_stream)
+    stream.synchronize()
+    dt = time.perf_counter() - t0
+    for s, o in zip(reqs, outs):
+        pool.put(s["width"], s["height"], o)
+    return dt
+
+
+def pct(v, q):
+    v = sorted(v)
+    return v[min(len(v) - 1, int(round(q * (len(v) - 1))))]
+
+
+def serving_section(local, n_sat=256, n_stream=600, rates=(1.0,)):
+    """Served vs back-to-back frames/s on a burst of the serving mix, then Poisson
+    arrivals at the given fractions of the measured saturation rate."""
+    import numpy as np
+    import torch
+
+    from paper_2303_14827_gb300 import binding, scenes
+    stream_reqs = [s for _, s in scenes.serving_stream(seed=2, n=max(n_sat, n_stream))]
+    pool = OutputPool(f"cuda:{local}")
+    ctx = binding.dqj_create(local)
+    try:
+        warm = stream_reqs[:32]
+        burst = stream_reqs[:n_sat]
+        pool.prefill(burst)
+        served_run(ctx, warm, [0.0] * len(warm), pool)
+        plain_back_to_back(ctx, warm, pool, torch.cuda.current_stream(local))
+        s0 = binding.dqj_serve_stats(ctx)
+        _, t_served = served_run(ctx, burst, [0.0] * len(burst), pool)
+        s1 = binding.dqj_serve_stats(ctx)
+        t_plain = plain_back_to_back(ctx, burst, pool, torch.cuda.current_stream(local))
+        sat = len(burst) / t_served
+        out = {"requests_burst": len(burst), "served_frames_per_s": sat,
+               "plain_back_to_back_frames_per_s": len(burst) / t_plain,
+               "served_over_plain": t_plain / t_served,
+               "burst_scheduler": {k: s1[k] - s0[k] for k in s1}, "poisson": []}
+        rng = np.random.default_rng(2)
+        gaps = rng.exponential(1.0, n_stream)
+        reqs = stream_reqs[:n_stream]
+        for f in rates:
+            arr = np.cumsum(gaps / (f * sat)).tolist()
+            lat, span = served_run(ctx, reqs, arr, pool)
+            out["poisson"].append({"offered_fraction_of_saturation": f, "requests": len(reqs),
+                                   "p50_ms": 1e3 * pct(lat, 0.50), "p99_ms": 1e3 * pct(lat, 0.99),
+                                   "achieved_frames_per_s": len(reqs) / span})
+        out["output_pool_misses"] = pool.misses
+        out["scheduler"] = binding.dqj_serve_stats(ctx)
+        return out
+    finally:
+        binding.dqj_destroy(ctx)
+
+
+def batch_section(local, n=64):
+    """The 64 mixed frames (random slices, resolutions, max_iter) as one served
+    batch in the persistent launch vs back to back, with autotuned tiles."""
+    import torch
+
+    from paper_2303_14827_gb300 import binding, scenes
+    reqs = scenes.batch_scenes(seed=1, n=n)
+    pool = OutputPool(f"cuda:{local}")
+    ctx = binding.dqj_create(local)
+    try:
+        binding.dqj_autotune(ctx, 0)
+        pool.prefill(reqs)
+        served_run(ctx, reqs[:8], [0.0] * 8, pool)
+        _, t_served = served_run(ctx, reqs, [0.0] * n, pool)
+        t_plain = plain_back_to_back(ctx, reqs, pool, torch.cuda.current_stream(local))
+        return {"frames": n, "served_frames_per_s": n / t_served, "plain_back_to_back_frames_per_s": n / t_plain,
+                "served_over_plain": t_plain / t_served}
+    finally:
+        binding.dqj_destroy(ctx)
+
+
+def run_serve_only(args, world, rank, local):
+    """C5: Poisson stream of render requests at offered rates relative to the
+    measured saturation throughput (one JSON line)."""
+    import torch
+    torch.cuda.set_device(local)
+    from paper_2303_14827_gb300 import binding
+    binding.load()
+    res = serving_section(local, n_sat=min(512, args.requests), n_stream=args.requests,
+                          rates=(0.5, 0.8, 1.0, 1.2))
+    one = next(p for p in res["poisson"] if p["offered_fraction_of_saturation"] == 1.0)
+    line = {"metric": "served p50/p99 latency (ms) and frames/s", "value": one["achieved_frames_per_s"],
+            "unit": "frames/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+            "config": {"workload": "Poisson stream: 256^2/512^2/1024^2/1920x1080 at 0.4/0.3/0.2/0.1, max_iter 8..32, "
+                                   "c random walk (sigma 0.01) from the default c, 512 march + 10 bisect, FP32, "
+                                   "16 GiB budget"},
+            "served": res}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
 
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
@@ -360,12 +549,17 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=60.0)
+    ap.add_argument("--no-serve", action="store_true", help="skip the served/batch sections")
+    ap.add_argument("--serve", action="store_true", help="only the Poisson serving benchmark")
+    ap.add_argument("--requests", type=int, default=10000)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "dqj":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     world, rank, local = dist_init()
     if args.impl == "reference":
         rc = run_reference(args, world, rank)
+    elif args.serve:
+        rc = run_serve_only(args, world, rank, local)
     else:
         rc = run_gpu(args, world, rank, local)
     if world > 1:

@@ -180,11 +180,23 @@ dqj_status dqj_render(dqj_ctx *ctx, const dqj_params *p, const dqj_outputs *out,
 dqj_status dqj_render_host(dqj_ctx *ctx, const dqj_params *p, const dqj_outputs *host_out);
 
 /* Serving: queue a request and return a ticket at once.  Outputs are
- * caller-owned device memory that must stay valid until dqj_poll reports done.
+ * caller-owned device memory that must stay valid until dqj_poll reports done
+ * and must have no pending work on any stream at submit: the library writes
+ * them from its own streams, unordered with the caller's.
  * Requests are admitted to the GPU while their footprint fits the context's
  * memory budget; admitted requests run together in one persistent launch.
  * DQJ_ERR_BUSY when max_pending requests are queued and not yet admitted. */
 dqj_status dqj_submit(dqj_ctx *ctx, const dqj_params *p, const dqj_outputs *out, dqj_ticket *ticket);
+
+/* Serving counters since the context started serving, DQJ_NSERVE_STATS int64
+ * values (all 0 before the first dqj_submit):
+ *   [0] persistent launches      [1] launches stopped to recycle control blocks
+ *   [2] requests run in the persistent launch   [3] requests run as plain frames
+ *   [4] admission batches        [5] host nanoseconds spent admitting batches
+ *   [6] requests completed       [7] scheduler loop iterations
+ * An interface of this library (observability); the paper has no counterpart. */
+#define DQJ_NSERVE_STATS 8
+dqj_status dqj_serve_stats(dqj_ctx *ctx, int64_t *out);
 
 /* Non-blocking completion check.  *done = 1 and *result = the request's status
  * once finished; the ticket is then consumed (a second poll: DQJ_ERR_NOT_FOUND). */
@@ -196,6 +208,22 @@ dqj_status dqj_poll(dqj_ctx *ctx, dqj_ticket ticket, int *done, dqj_status *resu
  * running; their device memory is then left allocated rather than freed under a
  * kernel that may still use it. */
 dqj_status dqj_destroy(dqj_ctx *ctx);
+
+/* Autotuning of the march tile shape (an interface of this library; the paper
+ * has no counterpart).  For each of the first max_classes frame-size classes
+ * (<= 256^2, <= 512^2, <= 1024^2, larger; 0 = all four) and each iteration bucket
+ * (max_iter <= 12, <= 20, <= 28, larger) renders a probe frame with every
+ * candidate shape of the paired FP32 march (8x8, 16x4, 4x16, 32x2, 64x1 rays),
+ * keeps the fastest (CUDA events, best of three) for later renders and served
+ * requests on this context, and writes the table to the cache file (the
+ * dqj_config path, else DQJ_AUTOTUNE_CACHE, else none).  dqj_create loads a
+ * cache written on the same device model.  Blocking; allocates ~50 MB of
+ * temporary planes. */
+dqj_status dqj_autotune(dqj_ctx *ctx, int32_t max_classes);
+
+/* The march kernel variant (0 one ray per lane, 1 two rays per lane) and tile
+ * shape this context would use for p. */
+dqj_status dqj_tile_shape(dqj_ctx *ctx, const dqj_params *p, int32_t *variant, int32_t *tile_w, int32_t *tile_h);
 
 /* Profiling: with ring_frames > 0 (at most 4096), every later render on this
  * context records CUDA events on its own stream before its first pass and after

@@ -122,8 +122,12 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         L.dqj_last_error.argtypes = []
         L.dqj_fma_peak.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P(ctypes.c_double)]
         L.dqj_render_noalloc.argtypes = [P(dqj_params), P(dqj_outputs), ctypes.c_void_p]
+        L.dqj_autotune.argtypes = [ctypes.c_void_p, ctypes.c_int32]
+        L.dqj_tile_shape.argtypes = [ctypes.c_void_p, P(dqj_params), P(ctypes.c_int32), P(ctypes.c_int32),
+                                     P(ctypes.c_int32)]
         L.dqj_set_profiling.argtypes = [ctypes.c_void_p, ctypes.c_int32]
         L.dqj_pass_ms.argtypes = [ctypes.c_void_p, ctypes.c_int32, P(ctypes.c_float)]
+        L.dqj_serve_stats.argtypes = [ctypes.c_void_p, P(ctypes.c_int64)]
         for name in declared_symbols():
             fn = getattr(L, name)
             if name != "dqj_last_error":
@@ -246,6 +250,20 @@ def dqj_poll(ctx: int, ticket: int):
     return bool(done.value), int(res.value)
 
 
+def dqj_autotune(ctx: int, max_classes: int = 0) -> None:
+    """Pick the fastest march tile shape per frame-size class and iteration bucket."""
+    check(load().dqj_autotune(ctypes.c_void_p(ctx), int(max_classes)))
+
+
+def dqj_tile_shape(ctx: int, scene: dict):
+    """(variant, tile_w, tile_h) the context would use for the scene."""
+    p = make_params(scene)
+    v, w, h = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    check(load().dqj_tile_shape(ctypes.c_void_p(ctx), ctypes.byref(p), ctypes.byref(v), ctypes.byref(w),
+                                ctypes.byref(h)))
+    return v.value, w.value, h.value
+
+
 def dqj_set_profiling(ctx: int, ring_frames: int) -> None:
     check(load().dqj_set_profiling(ctypes.c_void_p(ctx), int(ring_frames)))
 
@@ -256,6 +274,16 @@ def dqj_pass_ms(ctx: int, frames: int) -> list:
     ms = (ctypes.c_float * (4 * frames))()
     check(load().dqj_pass_ms(ctypes.c_void_p(ctx), int(frames), ms))
     return [list(ms[4 * i:4 * i + 4]) for i in range(frames)]
+
+
+SERVE_STAT_NAMES = ("launches", "restarts", "packed", "plain", "batches", "admit_ns", "completed", "loops")
+
+
+def dqj_serve_stats(ctx: int) -> dict:
+    """Serving counters of a context (see dqj_serve_stats in dqj.h)."""
+    v = (ctypes.c_int64 * len(SERVE_STAT_NAMES))()
+    check(load().dqj_serve_stats(ctypes.c_void_p(ctx), v))
+    return dict(zip(SERVE_STAT_NAMES, list(v)))
 
 
 def dqj_fma_peak(device: int = 0, variant: int = 0, launches: int = 3) -> float:
@@ -278,7 +306,7 @@ def alloc_outputs(width: int, height: int, device="cuda", pitch_px: int | None =
         "rgba": torch.empty((height, pitch, 4), dtype=torch.uint8, device=device),
     }
     if stats:
-        t["stats"] = torch.zeros(DQJ_NSTATS, dtype=torch.int64, device=device)
+        t["stats"] = torch.empty(DQJ_NSTATS, dtype=torch.int64, device=device)  # every entry is written
     t["pitch_px"] = pitch
     return t
 

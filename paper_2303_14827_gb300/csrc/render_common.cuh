@@ -289,7 +289,7 @@ __device__ __forceinline__ void bisect_chunk(const FrameDesc &fd, const Scratch 
     const unsigned idx = base + lane;
     const bool part = idx < nhits;
     int4 e = make_int4(0, 0, 0, 0);
-    if (part) e = sc.hits[idx];
+    if (part) e = __ldcg(sc.hits + idx);  // L2: the list may be rewritten within one serving launch
     const int pixel = e.x, k_first = e.y;
     const int x = pixel % fd.W, y = pixel / fd.W;
     T d[3] = {T(0), T(0), T(1)};

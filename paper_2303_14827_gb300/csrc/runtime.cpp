@@ -227,11 +227,14 @@ void pick_tile_shape(dqj_ctx *ctx, const dqj_params &p, int &variant, int &tw, i
     th = variant >= 1 ? 8 : 4;
     const int64_t px = (int64_t)p.width * p.height;
     const int cls = px <= 65536 ? 0 : px <= 262144 ? 1 : px <= 1048576 ? 2 : 3;
-    const int key = (variant * 4 + cls) * 4 + (p.max_iter <= 12 ? 0 : p.max_iter <= 20 ? 1 : p.max_iter <= 28 ? 2 : 3);
-    auto it = ctx->tiles.find(key);
-    if (it != ctx->tiles.end()) {
-        tw = it->second.first;
-        th = it->second.second;
+    const int bucket = p.max_iter <= 12 ? 0 : p.max_iter <= 20 ? 1 : p.max_iter <= 28 ? 2 : 3;
+    {
+        std::lock_guard<std::mutex> lk(ctx->tiles_mu);
+        auto it = ctx->tiles.find(tile_key(variant, cls, bucket));
+        if (it != ctx->tiles.end()) {
+            tw = it->second.first;
+            th = it->second.second;
+        }
     }
     // a warp covers 32 rays (one per lane) or 64 (two per lane)
     if (tw < 1 || th < 1 || tw * th != (variant >= 1 ? 64 : 32)) {
@@ -388,6 +391,7 @@ dqj_status dqj_create(const dqj_config *cfg, dqj_ctx **out)
         delete ctx;
         return s;
     }
+    load_tile_cache(ctx);
     *out = ctx;
     return DQJ_OK;
 }

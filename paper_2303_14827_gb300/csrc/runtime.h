@@ -57,6 +57,7 @@ struct dqj_ctx {
     int64_t *host_stats_dev = nullptr;
     // tile shapes chosen by the autotuner, keyed by (pixel-count class, iter bucket)
     std::map<int, std::pair<int, int>> tiles;
+    std::mutex tiles_mu;             // guards tiles (read by the serving thread too)
     dqj::ServeState *serve = nullptr;
     // profiling ring: ring_frames x 5 events, next slot, renders recorded
     std::vector<cudaEvent_t> ev;
@@ -67,4 +68,8 @@ struct dqj_ctx {
 namespace dqj {
 // March kernel variant and tile shape for a frame (autotuned choice or default).
 void pick_tile_shape(dqj_ctx *ctx, const dqj_params &p, int &variant, int &tw, int &th);
+// Autotuner cache (autotune.cpp): key of a (variant, size class, iteration bucket)
+// and loading of the cache file named by the context or DQJ_AUTOTUNE_CACHE.
+int tile_key(int variant, int size_class, int bucket);
+void load_tile_cache(dqj_ctx *ctx);
 }  // namespace dqj

@@ -15,10 +15,13 @@
 // use a CPU-only mock whose completion delay, allocation failure or
 // never-completing behaviour is set from the environment, so the admission,
 // budget, BUSY, TIMEOUT and CANCELLED paths are testable without a GPU.
+#include <algorithm>
 #include <chrono>
+#include <deque>
 #include <cstdlib>
 #include <cstring>
 #include <memory>
+#include <vector>
 
 #include "runtime.h"
 #include "serve_internal.h"
@@ -44,6 +47,7 @@ struct Request {
     uint64_t footprint = 0;
     bool packed = false;     // runs in the persistent launch
     int slot = -1;
+    unsigned block = ~0u;    // control block of a packed request
     uint64_t seq = 0;
     // device resources
     void *scratch = nullptr;
@@ -64,10 +68,14 @@ uint64_t scratch_bytes(const dqj_params &p, bool packed)
     return b;
 }
 
+// Per-request bookkeeping counted against the budget (control block and slot).
+constexpr uint64_t kRequestOverhead = 2048;
+static_assert(sizeof(ReqBlock) + sizeof(ServeSlot) <= kRequestOverhead, "request overhead");
+
 uint64_t footprint(const dqj_params &p, bool packed)
 {
     const uint64_t px = (uint64_t)p.width * (uint64_t)p.height;
-    return px * 24 + scratch_bytes(p, packed) + sizeof(ServeSlot);
+    return px * 24 + scratch_bytes(p, packed) + kRequestOverhead;
 }
 
 // -------------------------------------------------------------------------
@@ -75,11 +83,19 @@ uint64_t footprint(const dqj_params &p, bool packed)
 // -------------------------------------------------------------------------
 struct Backend {
     virtual ~Backend() = default;
-    virtual dqj_status admit(Request &r) = 0;     // start running r (slot already chosen when packed)
+    // Start running a batch of requests (slots already chosen for packed ones);
+    // writes each request's status into st[i].
+    virtual void admit(Request *const *rs, int n, dqj_status *st) = 0;
     virtual int poll(Request &r) = 0;             // 1 done, 0 running, -1 failed (message set)
     virtual dqj_status kick(bool packed_active) = 0;
+    virtual void hold(bool on) = 0;               // the host has queued or running work
     virtual void release(Request &r) = 0;
     virtual dqj_status shutdown(int64_t timeout_ms) = 0;
+    virtual void launch_counts(int64_t &launches, int64_t &restarts) const
+    {
+        launches = 0;
+        restarts = 0;
+    }
 };
 
 class GpuBackend : public Backend {
@@ -91,48 +107,93 @@ class GpuBackend : public Backend {
     {
         cudaError_t e = cudaSetDevice(ctx_->device);
         if (e == cudaSuccess) e = cudaMalloc(&d_slots_, sizeof(ServeSlot) * kMaxSlots);
-        if (e == cudaSuccess) e = cudaMemset(d_slots_, 0, sizeof(ServeSlot) * kMaxSlots);
-        if (e == cudaSuccess) e = cudaHostAlloc(&h_flags_, sizeof(unsigned) * (kMaxSlots + 1), cudaHostAllocMapped);
+        if (e == cudaSuccess) e = cudaMalloc(&d_blocks_, sizeof(ReqBlock) * kReqBlocks);
+        if (e == cudaSuccess) e = cudaMalloc(&d_exit_, 256);
+        if (e == cudaSuccess) e = cudaMemset(d_blocks_, 0, sizeof(ReqBlock) * kReqBlocks);
+        if (e == cudaSuccess) e = cudaHostAlloc(&h_flags_, sizeof(unsigned) * (kMaxSlots + 2), cudaHostAllocMapped);
         if (e == cudaSuccess) {
-            std::memset(h_flags_, 0, sizeof(unsigned) * (kMaxSlots + 1));
+            std::memset(h_flags_, 0, sizeof(unsigned) * (kMaxSlots + 2));
+            h_flags_[kMaxSlots] = 1;  // source of the host's exit request
             e = cudaHostGetDevicePointer(reinterpret_cast<void **>(&d_flags_), h_flags_, 0);
         }
-        if (e == cudaSuccess) e = cudaHostAlloc(&h_stage_, sizeof(ServeSlot) * kMaxSlots, cudaHostAllocDefault);
+        if (e == cudaSuccess) e = cudaHostAlloc(&h_slots_, sizeof(ServeSlot) * kMaxSlots, cudaHostAllocDefault);
+        if (e == cudaSuccess) e = cudaHostAlloc(&h_blocks_, sizeof(ReqBlock) * kReqBlocks, cudaHostAllocDefault);
+        if (e == cudaSuccess) {
+            std::memset(h_slots_, 0, sizeof(ServeSlot) * kMaxSlots);
+            for (int s = 0; s < kMaxSlots; ++s) h_slots_[s].block = ~0u;  // no block
+            e = cudaMemcpy(d_slots_, h_slots_, sizeof(ServeSlot) * kMaxSlots, cudaMemcpyHostToDevice);
+        }
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&kstream_, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cstream_, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&pstream_, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&kevent_, cudaEventDisableTiming);
         if (e != cudaSuccess) return cuda_fail(e, "serve: init");
+        for (unsigned b = 0; b < (unsigned)kReqBlocks; ++b) free_blocks_.push_back({b, 0});
+        for (int s = 0; s < kMaxSlots; ++s) slot_block_[s] = ~0u;
         idle_ns_ = (unsigned long long)env_int("DQJ_SERVE_IDLE_US", 2000) * 1000ull;
         return DQJ_OK;
     }
 
-    dqj_status admit(Request &r) override
+    // Packed requests: write their control blocks, wait for the copies, then
+    // publish the slots.  Plain requests: enqueue an ordinary frame.
+    void admit(Request *const *rs, int n, dqj_status *status) override
     {
         cudaError_t e = cudaSetDevice(ctx_->device);
-        if (e != cudaSuccess) return cuda_fail(e, "serve: cudaSetDevice");
-        const uint64_t px = (uint64_t)r.p.width * (uint64_t)r.p.height;
-        const uint64_t sb = scratch_bytes(r.p, r.packed);
-        cudaStream_t st = r.packed ? cstream_ : pstream_;
-        e = cudaMallocAsync(&r.scratch, sb, st);
-        if (e != cudaSuccess) return cuda_fail(e, "serve: scratch");
-        e = cudaMemsetAsync(r.scratch, 0, 256, st);
-        if (e != cudaSuccess) return cuda_fail(e, "serve: clear counters");
-        char *b = static_cast<char *>(r.scratch);
-        Scratch sc{};
-        sc.ctr = reinterpret_cast<Counters *>(b);
-        sc.hits = reinterpret_cast<int4 *>(b + 256);
-        sc.hit_cap = (uint32_t)px;
-        if (!r.packed && r.p.precision == DQJ_FP32_RECHECK) {
-            char *q = b + 256 + px * sizeof(int4);
-            sc.queue = reinterpret_cast<int4 *>(q);
-            sc.queue_cap = (uint32_t)(3 * px);
-            sc.dirty_flag = reinterpret_cast<uint32_t *>(q + 3 * px * sizeof(int4));
-            sc.dirty_list = reinterpret_cast<int32_t *>(q + 3 * px * sizeof(int4) + px * 4);
-            sc.dirty_cap = (uint32_t)px;
-            e = cudaMemsetAsync(sc.dirty_flag, 0, px * 4, st);
-            if (e != cudaSuccess) return cuda_fail(e, "serve: clear flags");
+        for (int i = 0; i < n; ++i) status[i] = e == cudaSuccess ? DQJ_OK : cuda_fail(e, "serve: cudaSetDevice");
+        if (e != cudaSuccess) return;
+        std::vector<unsigned> staged;  // blocks whose bodies were staged, in request order
+        bool packed_any = false;
+        for (int i = 0; i < n; ++i) {
+            Request &r = *rs[i];
+            status[i] = r.packed ? stage_packed(r) : launch_plain(r);
+            if (r.packed && status[i] == DQJ_OK) {
+                staged.push_back(r.block);
+                packed_any = true;
+            }
         }
+        if (!packed_any) return;
+        // bodies: one copy per run of consecutive block indices
+        std::sort(staged.begin(), staged.end());
+        for (size_t i = 0; i < staged.size() && e == cudaSuccess;) {
+            size_t j = i + 1;
+            while (j < staged.size() && staged[j] == staged[j - 1] + 1) ++j;
+            e = cudaMemcpyAsync(d_blocks_ + staged[i], h_blocks_ + staged[i], sizeof(ReqBlock) * (j - i),
+                                cudaMemcpyHostToDevice, cstream_);
+            i = j;
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(cstream_);  // bodies visible before any slot names them
+        if (e == cudaSuccess) {
+            for (int i = 0; i < n; ++i) {
+                Request &r = *rs[i];
+                if (!r.packed || status[i] != DQJ_OK) continue;
+                retire_block(slot_block_[r.slot]);  // the slot's previous request's block
+                slot_block_[r.slot] = r.block;
+                h_slots_[r.slot].block = r.block;
+                h_slots_[r.slot].seq = r.seq;
+            }
+            // the host holds the only copy that changes: rewrite the whole table
+            e = cudaMemcpyAsync(d_slots_, h_slots_, sizeof(ServeSlot) * kMaxSlots, cudaMemcpyHostToDevice, cstream_);
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(cstream_);
+        if (e != cudaSuccess) {
+            const dqj_status f = cuda_fail(e, "serve: publish requests");
+            for (int i = 0; i < n; ++i) {
+                Request &r = *rs[i];
+                if (!r.packed) continue;
+                if (status[i] == DQJ_OK && slot_block_[r.slot] != r.block) retire_block(r.block);  // never published
+                status[i] = f;
+            }
+        }
+    }
+
+    void hold(bool on) override
+    {
+        if (h_flags_) *reinterpret_cast<volatile unsigned *>(&h_flags_[kMaxSlots + 1]) = on ? 1u : 0u;
+    }
+
+  private:
+    FrameDesc frame_of(Request &r)
+    {
         int variant, tw, th;
         pick_tile_shape(ctx_, r.p, variant, tw, th);
         FrameDesc fd;
@@ -145,45 +206,125 @@ class GpuBackend : public Backend {
         fd.rgba = r.out.rgba;
         fd.stats = r.out.stats;
         fd.epoch = 1;
-        if (!r.packed) {
-            e = launch_frame(fd, sc, st, ctx_->num_sms);
-            if (e == cudaSuccess && r.out.stats)
-                e = cudaMemcpyAsync(r.out.stats, sc.ctr->stats, DQJ_NSTATS * sizeof(int64_t), cudaMemcpyDeviceToDevice,
-                                    st);
-            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r.done_ev, cudaEventDisableTiming);
-            if (e == cudaSuccess) e = cudaEventRecord(r.done_ev, st);
-            if (e != cudaSuccess) return cuda_fail(e, "serve: frame launch");
-            return DQJ_OK;
+        return fd;
+    }
+
+    // Launch ids: a block retired while launch L (the last one started) may run
+    // is reusable once launch L has exited.
+    void update_completed()
+    {
+        if (launched_ && completed_ < launches_ && cudaEventQuery(kevent_) == cudaSuccess) completed_ = launches_;
+    }
+
+    void retire_block(unsigned b)
+    {
+        if (b < (unsigned)kReqBlocks) free_blocks_.push_back({b, launches_});
+    }
+
+    // A control block that no launch can still be reading.  When every free block
+    // may still be seen by the running launch, stop it (claimed items finish; the
+    // next launch continues from the claim counters) and wait for it to exit.
+    dqj_status take_block(unsigned &b)
+    {
+        update_completed();
+        if (free_blocks_.empty()) return fail(DQJ_ERR_NOMEM, "serve: control-block pool exhausted");
+        if (free_blocks_.front().second > completed_) {
+            const dqj_status s = stop_launch(10000);
+            if (s != DQJ_OK) return s;
+            ++restarts_;
         }
-        // packed: write the slot (seq = 0, body, then seq) -- see serve.cu
-        const unsigned gen = (unsigned)r.seq;
-        const unsigned long long tag = (unsigned long long)gen << 32;
-        ServeSlot &h = h_stage_[r.slot];
-        std::memset(&h, 0, sizeof h);
-        h.seq = 0;
-        h.phase = tag | kPhaseMarch;
-        h.tile_claim = h.tile_done = h.hit_claim = h.hit_done = tag;
-        h.ntiles = (unsigned)fd.tiles_x * (unsigned)fd.tiles_y;
-        h.hit_total = 0;
-        h.sc = sc;
-        h.fd = fd;
-        ServeSlot *d = d_slots_ + r.slot;
-        e = cudaMemsetAsync(&d->seq, 0, sizeof(unsigned long long), cstream_);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(reinterpret_cast<char *>(d) + sizeof(unsigned long long),
-                                reinterpret_cast<char *>(&h) + sizeof(unsigned long long),
-                                sizeof(ServeSlot) - sizeof(unsigned long long), cudaMemcpyHostToDevice, cstream_);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(cstream_);
-        if (e == cudaSuccess) {
-            seq_stage_[r.slot] = r.seq;
-            e = cudaMemcpyAsync(&d->seq, &seq_stage_[r.slot], sizeof(unsigned long long), cudaMemcpyHostToDevice,
-                                cstream_);
-        }
-        if (e == cudaSuccess) e = cudaStreamSynchronize(cstream_);
-        if (e != cudaSuccess) return cuda_fail(e, "serve: publish slot");
+        b = free_blocks_.front().first;
+        free_blocks_.pop_front();
         return DQJ_OK;
     }
 
+    // Raise the launch's exit flag with a copy-engine write (no SM needed while
+    // the persistent grid occupies them) and wait, bounded, for the launch to end.
+    dqj_status stop_launch(int64_t timeout_ms)
+    {
+        if (!launched_ || completed_ == launches_) return DQJ_OK;
+        cudaError_t e = cudaMemcpyAsync(d_exit_, &h_flags_[kMaxSlots], sizeof(unsigned), cudaMemcpyHostToDevice,
+                                        cstream_);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(cstream_);
+        if (e != cudaSuccess) return cuda_fail(e, "serve: exit request");
+        const auto t0 = clk::now();
+        for (;;) {
+            const cudaError_t q = cudaEventQuery(kevent_);
+            if (q == cudaSuccess) break;
+            if (q != cudaErrorNotReady) return cuda_fail(q, "serve: persistent kernel");
+            if (clk::now() - t0 > std::chrono::milliseconds(timeout_ms))
+                return fail(DQJ_ERR_TIMEOUT, "serve: persistent kernel did not stop in time");
+            std::this_thread::sleep_for(std::chrono::microseconds(20));
+        }
+        completed_ = launches_;
+        return DQJ_OK;
+    }
+
+    // Stage a packed request's control block in host memory.
+    dqj_status stage_packed(Request &r)
+    {
+        const uint64_t px = (uint64_t)r.p.width * (uint64_t)r.p.height;
+        const uint64_t need = px * sizeof(int4);
+        cudaError_t e = cudaSuccess;
+        if (slot_cap_[r.slot] < need) {  // grow-only hit list per slot
+            if (slot_scratch_[r.slot]) e = cudaFreeAsync(slot_scratch_[r.slot], cstream_);
+            slot_scratch_[r.slot] = nullptr;
+            slot_cap_[r.slot] = 0;
+            if (e == cudaSuccess) e = cudaMallocAsync(&slot_scratch_[r.slot], need, cstream_);
+            if (e != cudaSuccess) return cuda_fail(e, "serve: slot hit list");
+            slot_cap_[r.slot] = need;
+        }
+        unsigned bi = 0;
+        dqj_status s = take_block(bi);
+        if (s != DQJ_OK) return s;
+        r.block = bi;
+        ReqBlock &h = h_blocks_[bi];
+        std::memset(&h, 0, sizeof h);
+        h.phase = kPhaseMarch;
+        h.fd = frame_of(r);
+        h.ntiles = (unsigned)h.fd.tiles_x * (unsigned)h.fd.tiles_y;
+        h.slot = (unsigned)r.slot;
+        h.gen = (unsigned)r.seq;
+        h.sc.ctr = &d_blocks_[bi].ctr;
+        h.sc.hits = static_cast<int4 *>(slot_scratch_[r.slot]);
+        h.sc.hit_cap = (uint32_t)px;
+        return DQJ_OK;
+    }
+
+    // Other precisions and modes: an ordinary frame on the serving stream.
+    dqj_status launch_plain(Request &r)
+    {
+        const uint64_t px = (uint64_t)r.p.width * (uint64_t)r.p.height;
+        cudaError_t e = cudaMallocAsync(&r.scratch, scratch_bytes(r.p, false), pstream_);
+        if (e == cudaSuccess) e = cudaMemsetAsync(r.scratch, 0, 256, pstream_);
+        if (e != cudaSuccess) return cuda_fail(e, "serve: scratch");
+        char *b = static_cast<char *>(r.scratch);
+        Scratch sc{};
+        sc.ctr = reinterpret_cast<Counters *>(b);
+        sc.hits = reinterpret_cast<int4 *>(b + 256);
+        sc.hit_cap = (uint32_t)px;
+        if (r.p.precision == DQJ_FP32_RECHECK) {
+            char *q = b + 256 + px * sizeof(int4);
+            sc.queue = reinterpret_cast<int4 *>(q);
+            sc.queue_cap = (uint32_t)(3 * px);
+            sc.dirty_flag = reinterpret_cast<uint32_t *>(q + 3 * px * sizeof(int4));
+            sc.dirty_list = reinterpret_cast<int32_t *>(q + 3 * px * sizeof(int4) + px * 4);
+            sc.dirty_cap = (uint32_t)px;
+            e = cudaMemsetAsync(sc.dirty_flag, 0, px * 4, pstream_);
+            if (e != cudaSuccess) return cuda_fail(e, "serve: clear flags");
+        }
+        const FrameDesc fd = frame_of(r);
+        e = launch_frame(fd, sc, pstream_, ctx_->num_sms);
+        if (e == cudaSuccess && r.out.stats)
+            e = cudaMemcpyAsync(r.out.stats, sc.ctr->stats, DQJ_NSTATS * sizeof(int64_t), cudaMemcpyDeviceToDevice,
+                                pstream_);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r.done_ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(r.done_ev, pstream_);
+        if (e != cudaSuccess) return cuda_fail(e, "serve: frame launch");
+        return DQJ_OK;
+    }
+
+  public:
     int poll(Request &r) override
     {
         if (r.packed) {
@@ -212,10 +353,11 @@ class GpuBackend : public Backend {
             const cudaError_t q = cudaEventQuery(kevent_);
             if (q == cudaErrorNotReady) return DQJ_OK;  // still running: it picks up new slots
             if (q != cudaSuccess) return cuda_fail(q, "serve: persistent kernel");
+            completed_ = launches_;
         }
         cudaError_t e = cudaSetDevice(ctx_->device);
-        ServeCtl ctl{d_slots_, d_flags_, d_flags_ + kMaxSlots, idle_ns_};
-        h_flags_[kMaxSlots] = 0;
+        ServeCtl ctl{d_slots_, d_blocks_, d_flags_, d_exit_, d_flags_ + kMaxSlots + 1, idle_ns_, 1000000000ull};
+        if (e == cudaSuccess) e = cudaMemsetAsync(d_exit_, 0, sizeof(unsigned), kstream_);  // ordered before the launch
         if (e == cudaSuccess) e = serve_launch(ctl, ctx_->num_sms, kstream_);
         if (e == cudaSuccess) e = cudaEventRecord(kevent_, kstream_);
         if (e != cudaSuccess) return cuda_fail(e, "serve: launch");
@@ -231,33 +373,18 @@ class GpuBackend : public Backend {
             cudaEventDestroy(r.done_ev);
             r.done_ev = nullptr;
         }
-        if (r.scratch) {
-            cudaFreeAsync(r.scratch, r.packed ? cstream_ : pstream_);
+        if (r.scratch) {  // plain-path scratch; packed requests use their slot's hit list
+            cudaFreeAsync(r.scratch, pstream_);
             r.scratch = nullptr;
         }
+        // a packed request's control block stays named by its slot until the
+        // slot is republished (admit retires it then)
     }
 
     dqj_status shutdown(int64_t timeout_ms) override
     {
         cudaSetDevice(ctx_->device);
-        if (h_flags_) *reinterpret_cast<volatile unsigned *>(&h_flags_[kMaxSlots]) = 1;  // stop
-        dqj_status st = DQJ_OK;
-        if (launched_) {
-            const auto t0 = clk::now();
-            for (;;) {
-                const cudaError_t q = cudaEventQuery(kevent_);
-                if (q == cudaSuccess) break;
-                if (q != cudaErrorNotReady) {
-                    st = cuda_fail(q, "serve: persistent kernel");
-                    break;
-                }
-                if (clk::now() - t0 > std::chrono::milliseconds(timeout_ms)) {
-                    st = fail(DQJ_ERR_TIMEOUT, "serve: persistent kernel did not stop in time");
-                    break;
-                }
-                std::this_thread::sleep_for(std::chrono::microseconds(100));
-            }
-        }
+        const dqj_status st = stop_launch(timeout_ms);
         if (st == DQJ_OK) {
             cudaStreamSynchronize(pstream_);
             cudaStreamSynchronize(cstream_);
@@ -265,15 +392,24 @@ class GpuBackend : public Backend {
         return st;
     }
 
-    uint64_t launches() const { return launches_; }
+    void launch_counts(int64_t &launches, int64_t &restarts) const override
+    {
+        launches = (int64_t)launches_;
+        restarts = (int64_t)restarts_;
+    }
 
   private:
     void free_all()
     {
         cudaSetDevice(ctx_->device);
+        for (auto &p : slot_scratch_)
+            if (p) cudaFree(p);
         if (d_slots_) cudaFree(d_slots_);
+        if (d_blocks_) cudaFree(d_blocks_);
+        if (d_exit_) cudaFree(d_exit_);
         if (h_flags_) cudaFreeHost(h_flags_);
-        if (h_stage_) cudaFreeHost(h_stage_);
+        if (h_slots_) cudaFreeHost(h_slots_);
+        if (h_blocks_) cudaFreeHost(h_blocks_);
         if (kevent_) cudaEventDestroy(kevent_);
         if (kstream_) cudaStreamDestroy(kstream_);
         if (cstream_) cudaStreamDestroy(cstream_);
@@ -281,14 +417,18 @@ class GpuBackend : public Backend {
     }
 
     dqj_ctx *ctx_;
-    ServeSlot *d_slots_ = nullptr;
-    ServeSlot *h_stage_ = nullptr;
-    unsigned long long seq_stage_[kMaxSlots] = {};
-    unsigned *h_flags_ = nullptr, *d_flags_ = nullptr;
+    ServeSlot *d_slots_ = nullptr, *h_slots_ = nullptr;  // h_slots_: the authoritative copy
+    ReqBlock *d_blocks_ = nullptr, *h_blocks_ = nullptr;
+    std::deque<std::pair<unsigned, uint64_t>> free_blocks_;  // (block, launch id when retired), oldest first
+    unsigned slot_block_[kMaxSlots] = {};
+    void *slot_scratch_[kMaxSlots] = {};
+    uint64_t slot_cap_[kMaxSlots] = {};
+    unsigned *h_flags_ = nullptr, *d_flags_ = nullptr;  // [0, kMaxSlots) done flags, [kMaxSlots] = 1, then hold
+    unsigned *d_exit_ = nullptr;
     cudaStream_t kstream_ = nullptr, cstream_ = nullptr, pstream_ = nullptr;
     cudaEvent_t kevent_ = nullptr;
     bool launched_ = false;
-    uint64_t launches_ = 0;
+    uint64_t launches_ = 0, completed_ = 0, restarts_ = 0;
     unsigned long long idle_ns_ = 0;
 };
 
@@ -304,13 +444,19 @@ class MockBackend : public Backend {
         nomem_ = f && std::strcmp(f, "nomem") == 0;
         hang_ = f && std::strcmp(f, "hang") == 0;
     }
-    dqj_status admit(Request &r) override
+    void admit(Request *const *rs, int n, dqj_status *st) override
     {
-        if (nomem_) return fail(DQJ_ERR_NOMEM, "serve (mock): injected allocation failure");
-        r.admitted = clk::now();
-        ++running_;
-        return DQJ_OK;
+        for (int i = 0; i < n; ++i) {
+            if (nomem_) {
+                st[i] = fail(DQJ_ERR_NOMEM, "serve (mock): injected allocation failure");
+                continue;
+            }
+            rs[i]->admitted = clk::now();
+            ++running_;
+            st[i] = DQJ_OK;
+        }
     }
+    void hold(bool) override {}
     int poll(Request &r) override
     {
         if (hang_) return 0;
@@ -352,6 +498,7 @@ struct ServeState {
     uint64_t next_seq = 1;
     bool draining = false, stop = false;
     std::thread thr;
+    int64_t n_packed = 0, n_plain = 0, n_batches = 0, admit_ns = 0, n_completed = 0, n_loops = 0;
 
     void complete(Request *r, dqj_status st)
     {
@@ -359,23 +506,30 @@ struct ServeState {
         if (r->slot >= 0) slot_req[r->slot] = nullptr;
         used -= r->footprint;
         finished[r->ticket] = st;
+        ++n_completed;
     }
 
     void loop()
     {
         std::unique_lock<std::mutex> lk(mu);
+        std::vector<Request *> batch;
+        std::vector<dqj_status> st;
         while (!stop) {
+            ++n_loops;
             // completions
             for (auto it = active.begin(); it != active.end();) {
-                const int s = backend->poll(*it->second);
+                Request *r = it->second.get();
+                const int s = r->seq ? backend->poll(*r) : 0;
                 if (s != 0) {
-                    complete(it->second.get(), s > 0 ? DQJ_OK : DQJ_ERR_CUDA);
+                    complete(r, s > 0 ? DQJ_OK : DQJ_ERR_CUDA);
                     it = active.erase(it);
                 } else {
                     ++it;
                 }
             }
-            // admissions, in arrival order, while the budget and a slot allow
+            // choose admissions in arrival order while the budget and a slot allow;
+            // they count as active (dqj_poll sees them) while being written
+            batch.clear();
             while (!draining && !pending.empty()) {
                 Request *r = pending.front().get();
                 if (used + r->footprint > ctx->cfg.mem_budget_bytes) break;
@@ -384,21 +538,35 @@ struct ServeState {
                     for (int s = 0; s < kMaxSlots && slot < 0; ++s)
                         if (!slot_req[s]) slot = s;
                     if (slot < 0) break;
+                    slot_req[slot] = r;
                 }
-                std::unique_ptr<Request> own = std::move(pending.front());
-                pending.pop_front();
                 r->slot = slot;
-                r->seq = next_seq++;
-                if ((unsigned)r->seq == 0) r->seq = next_seq++;  // generation 0 means "empty"
-                const dqj_status st = backend->admit(*r);
-                if (st != DQJ_OK) {
-                    backend->release(*r);
-                    finished[r->ticket] = st;
-                    continue;
-                }
-                if (slot >= 0) slot_req[slot] = r;
                 used += r->footprint;
-                active.emplace(r->ticket, std::move(own));
+                active.emplace(r->ticket, std::move(pending.front()));
+                pending.pop_front();
+                batch.push_back(r);
+            }
+            backend->hold(!pending.empty() || !active.empty());
+            if (!batch.empty()) {
+                for (Request *r : batch) {
+                    r->seq = next_seq++;
+                    if ((unsigned)r->seq == 0) r->seq = next_seq++;  // generation 0 means "empty"
+                }
+                // write the slots / launch the frames without holding the lock
+                st.assign(batch.size(), DQJ_OK);
+                lk.unlock();
+                const auto ta = clk::now();
+                backend->admit(batch.data(), (int)batch.size(), st.data());
+                const int64_t dt = std::chrono::duration_cast<std::chrono::nanoseconds>(clk::now() - ta).count();
+                lk.lock();
+                admit_ns += dt;
+                ++n_batches;
+                for (Request *r : batch) ++(r->packed ? n_packed : n_plain);
+                for (size_t i = 0; i < batch.size(); ++i) {
+                    if (st[i] == DQJ_OK) continue;
+                    complete(batch[i], st[i]);
+                    active.erase(batch[i]->ticket);
+                }
             }
             bool packed_active = false;
             for (auto &kv : active) packed_active = packed_active || kv.second->packed;
@@ -412,6 +580,7 @@ struct ServeState {
             else
                 cv.wait(lk, [&] { return stop || (!pending.empty() && !draining); });
         }
+        backend->hold(false);
     }
 };
 
@@ -470,6 +639,23 @@ dqj_status dqj_submit(dqj_ctx *ctx, const dqj_params *p, const dqj_outputs *out,
     *ticket = r->ticket;
     S.pending.push_back(std::move(r));
     S.cv.notify_all();
+    return DQJ_OK;
+}
+
+dqj_status dqj_serve_stats(dqj_ctx *ctx, int64_t *out)
+{
+    if (!ctx || !out) return fail(DQJ_ERR_INVALID, "ctx or out is NULL");
+    for (int i = 0; i < DQJ_NSERVE_STATS; ++i) out[i] = 0;
+    if (!ctx->serve) return DQJ_OK;
+    ServeState &S = *ctx->serve;
+    std::lock_guard<std::mutex> lk(S.mu);
+    S.backend->launch_counts(out[0], out[1]);
+    out[2] = S.n_packed;
+    out[3] = S.n_plain;
+    out[4] = S.n_batches;
+    out[5] = S.admit_ns;
+    out[6] = S.n_completed;
+    out[7] = S.n_loops;
     return DQJ_OK;
 }
 

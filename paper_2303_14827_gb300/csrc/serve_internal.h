@@ -7,33 +7,48 @@
 namespace dqj {
 
 constexpr int kMaxSlots = 64;        // requests resident on the device at once
+constexpr int kReqBlocks = 1024;     // request control blocks (see ReqBlock)
 constexpr int DQJ_NSTATS_DEV = 10;   // = DQJ_NSTATS
 
 enum : unsigned { kPhaseMarch = 0, kPhaseBisect = 1, kPhaseDone = 2 };
 
-// One resident request.  Words that warps update are generation-tagged: the high
-// 32 bits hold the request's generation (the low 32 bits of seq).
-struct alignas(16) ServeSlot {
-    unsigned long long seq;         // admission sequence; 0 while empty or being rewritten
-    unsigned long long phase;       // (gen << 32) | kPhase*
-    unsigned long long tile_claim;  // (gen << 32) | next march tile
-    unsigned long long tile_done;   // (gen << 32) | march tiles completed
-    unsigned long long hit_claim;   // (gen << 32) | next hit-list entry
-    unsigned long long hit_done;    // (gen << 32) | hit-list entries completed
+// Control block of one admitted request.  Written by the host before the
+// request is published and, apart from its counters, never changed afterwards.
+// The host hands a block to a new request only after every warp of the launch
+// that could have seen its previous request has exited, so a warp holding a
+// stale view finds only exhausted claim counters and can do no harm.
+struct alignas(128) ReqBlock {
+    unsigned long long tile_claim;  // next march tile (claims may run past ntiles)
+    unsigned long long tile_done;   // march tiles completed
+    unsigned long long hit_claim;   // next hit-list entry
+    unsigned long long hit_done;    // hit-list entries completed
+    unsigned phase;                 // kPhase*
     unsigned ntiles;                // march tiles of the frame
     unsigned hit_total;             // hit-list length, set when the march completes
-    unsigned pad[2];
-    Scratch sc;                     // the request's counters and hit list
+    unsigned slot;                  // slot the request occupies
+    unsigned gen;                   // generation reported through the slot's done flag
+    unsigned pad[3];
+    Counters ctr;                   // the request's counters (stats, hit_count)
+    Scratch sc;                     // sc.ctr = &ctr; sc.hits = the slot's hit buffer
     FrameDesc fd;                   // frame constants and caller's output planes
 };
-static_assert(sizeof(Scratch) % 16 == 0, "Scratch is copied as uint4");
 static_assert(sizeof(FrameDesc) % 16 == 0, "FrameDesc is copied as uint4");
+
+// One resident request: which control block, published by writing seq last.
+struct alignas(16) ServeSlot {
+    unsigned long long seq;         // admission sequence; 0 while empty
+    unsigned block;                 // index into the ReqBlock array
+    unsigned pad;
+};
 
 struct ServeCtl {
     ServeSlot *slots;               // device array of kMaxSlots
+    ReqBlock *blocks;               // device array of kReqBlocks
     unsigned *done_flags;           // mapped host memory: generation of the last finished request per slot
-    unsigned *stop;                 // mapped host memory: non-zero asks the kernel to exit
-    unsigned long long idle_ns;     // a warp with no work for this long exits
+    unsigned *exit_flag;            // device memory, 0 at launch: non-zero makes every warp exit
+    unsigned *hold;                 // mapped host memory: non-zero while the host has queued or running work
+    unsigned long long idle_ns;     // a warp with no work (and no hold) for this long ends the launch
+    unsigned long long hold_ns;     // ... and with hold set, after this long regardless
 };
 
 cudaError_t serve_launch(const ServeCtl &ctl, int num_sms, cudaStream_t st);

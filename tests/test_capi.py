@@ -1,6 +1,8 @@
 """CPU checks of the C ABI: the library loads, exports every function that
 include/dqj.h declares, its defaults match the single-frame scene, and host-side
 validation rejects bad parameter blocks with a message (no GPU needed)."""
+import re
+
 import numpy as np
 import pytest
 
@@ -64,3 +66,8 @@ def test_null_arguments_are_errors_not_crashes(lib):
     assert lib.dqj_destroy(None) == binding.DQJ_ERR_INVALID
     assert lib.dqj_render(None, None, None, None) == binding.DQJ_ERR_INVALID
     assert binding.last_error()
+
+
+def test_serve_stats_layout_matches_header():
+    text = open(binding.HEADER).read()
+    assert re.search(r"#define DQJ_NSERVE_STATS (\d+)", text).group(1) == str(len(binding.SERVE_STAT_NAMES))

@@ -16,11 +16,10 @@ pytestmark = pytest.mark.gpu
 
 
 def run_served(ctx, reqs, timeout=60.0):
-    outs, tickets = [], []
-    for s in reqs:
-        o = binding.alloc_outputs(s["width"], s["height"])
-        outs.append(o)
-        tickets.append(binding.dqj_submit(ctx, s, binding.outputs_of(o)))
+    import torch
+    outs = [binding.alloc_outputs(s["width"], s["height"]) for s in reqs]
+    torch.cuda.synchronize()  # the library writes outputs from its own streams
+    tickets = [binding.dqj_submit(ctx, s, binding.outputs_of(o)) for s, o in zip(reqs, outs)]
     pending = set(range(len(reqs)))
     status = {}
     t0 = time.time()
@@ -115,11 +114,41 @@ def test_budget_limited_admission_and_many_small_requests():
 
 
 def test_destroy_with_requests_in_flight():
+    import torch
     ctx = binding.dqj_create(0)
     outs = []
     for k in range(8):
         s = scenes.full_hd_scene(k % 5)
         o = binding.alloc_outputs(s["width"], s["height"])
+        torch.cuda.synchronize()
         outs.append(o)
         binding.dqj_submit(ctx, s, binding.outputs_of(o))
     binding.dqj_destroy(ctx)  # waits (bounded) for admitted requests, cancels queued ones
+
+
+def test_waves_with_idle_gaps_keep_full_speed():
+    """Requests arriving in waves separated by about the kernel's idle limit: a
+    launch must end as a whole, never leaving a few warps to serve the next wave."""
+    import torch
+    s = scenes.default_scene(width=256, height=256, max_iter=12)
+    ctx = binding.dqj_create(0)
+    try:
+        outs = [binding.alloc_outputs(256, 256) for _ in range(8)]
+        torch.cuda.synchronize()
+        t0 = time.time()
+        for wave in range(40):
+            tickets = [binding.dqj_submit(ctx, s, binding.outputs_of(o)) for o in outs]
+            for t in tickets:
+                while True:
+                    done, st = binding.dqj_poll(ctx, t)
+                    if done:
+                        assert st == binding.DQJ_OK
+                        break
+                    assert time.time() - t0 < 20.0, f"wave {wave} stalled"
+                    time.sleep(0.0002)
+            time.sleep(0.0015 + 0.0001 * (wave % 10))
+        assert time.time() - t0 < 20.0
+        stats = binding.dqj_serve_stats(ctx)
+        assert stats["completed"] == 320 and stats["packed"] == 320
+    finally:
+        binding.dqj_destroy(ctx)

@@ -137,3 +137,15 @@ def test_mock_context_cannot_render(mock_env):
         binding.dqj_render(ctx, scenes.default_scene(width=8, height=8), binding.make_outputs(pitch_px=8), 0)
     assert ei.value.status == binding.DQJ_ERR_INVALID
     binding.dqj_destroy(ctx)
+
+
+def test_serve_stats_count_admissions_and_completions(mock_env):
+    ctx = binding.dqj_create(MOCK)
+    assert binding.dqj_serve_stats(ctx) == {k: 0 for k in binding.SERVE_STAT_NAMES}
+    s = scenes.default_scene(width=16, height=16)
+    tickets = [binding.dqj_submit(ctx, s, binding.make_outputs(pitch_px=16)) for _ in range(7)]
+    wait_all(ctx, tickets)
+    st = binding.dqj_serve_stats(ctx)
+    assert st["completed"] == 7 and st["plain"] == 7 and st["packed"] == 0  # the mock runs no persistent launch
+    assert 1 <= st["batches"] <= 7 and st["launches"] == 0 and st["loops"] >= st["batches"]
+    binding.dqj_destroy(ctx)
