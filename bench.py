@@ -40,8 +40,8 @@ FLOPS_PER_ITER = 52          # specialised square + c + EUCLID8 modulus test, FM
 SM_MAX_MHZ = 2070.0
 FP32_LANES_PER_SM = 128
 WORKLOAD = "dq-julia 1920x1080, c~U[-0.8,0.8]^8 seeds 0-4, max_iter 16, 512 march + 10 bisect, FP32"
-KERNEL_SOURCES = ("paper_2303_14827_gb300/csrc/render.cu", "paper_2303_14827_gb300/csrc/dq_math.cuh",
-                  "paper_2303_14827_gb300/csrc/dqj_internal.h")
+KERNEL_SOURCES = ("paper_2303_14827_gb300/csrc/render.cu", "paper_2303_14827_gb300/csrc/render_common.cuh",
+                  "paper_2303_14827_gb300/csrc/dq_math.cuh", "paper_2303_14827_gb300/csrc/dqj_internal.h")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "march_kernel_1080p.md")
 
 
@@ -290,7 +290,7 @@ def run_gpu(args, world, rank, local):
     clocks = clk.summary()
     roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
             "frac": round(achieved / peak, 4), "traffic": recorded_traffic(),
-            "kernel": "march_kernel<float,ALGEBRAIC,EUCLID8>", "launches": len(march_ms),
+            "kernel": "march2_kernel<ALGEBRAIC,EUCLID8>", "launches": len(march_ms),
             "avg_launch_ms": round(sum(march_ms) / len(march_ms), 4),
             "flops_per_iter": FLOPS_PER_ITER,
             "peak_basis": f"{num_sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {SM_MAX_MHZ:.0f} MHz (max clock)"}
@@ -360,8 +360,9 @@ def run_gpu(args, world, rank, local):
 class OutputPool:
     """Reusable device output planes per resolution (caller-owned outputs must
     stay valid until the request completes).  Planes are allocated up front by
-    prefill: a device synchronize after an allocation would wait for the
-    persistent serving launch, so `misses` counts allocations made later."""
+    prefill; `misses` counts allocations made later.  After an allocation only
+    torch's own stream is synchronized (the library writes outputs from its own
+    streams): a device-wide synchronize would wait for the persistent launch."""
 
     def __init__(self, device):
         self.device = device
@@ -390,7 +391,7 @@ class OutputPool:
             return lst.pop()
         self.misses += 1
         o = self._alloc(w, h)
-        torch.cuda.synchronize(self.device)
+        torch.cuda.current_stream(self.device).synchronize()
         return o
 
     def put(self, w, h, o):
@@ -518,6 +519,84 @@ def batch_section(local, n=64):
         binding.dqj_destroy(ctx)
 
 
+def precision_section(local, reps=3):
+    """FP32, FP32 + FP64 recheck and all-FP64 renders of the workload frames (and
+    of the default c at 1920x1080, which has many hits): time per frame, recheck
+    rate, and the FP32 / FP32+recheck images against the all-FP64 GPU image
+    (hit/miss flips, iteration mismatches on agreeing pixels, depth error on
+    agreeing hits).  The FP64 render is itself held to the oracle by the tests."""
+    import torch
+
+    from paper_2303_14827_gb300 import binding, scenes
+    rows = [("seed%d" % k, scenes.full_hd_scene(k)) for k in SEEDS]
+    rows.append(("default_c_1080p", scenes.default_scene(width=1920, height=1080, max_iter=16, march_steps=512,
+                                                        bisect_steps=10)))
+    ctx = binding.dqj_create(local)
+    stream = torch.cuda.current_stream(local)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = []
+    try:
+        for name, base in rows:
+            W, H = base["width"], base["height"]
+            res = {}
+            for prec in (scenes.PRECISION_FP32, scenes.PRECISION_FP32_RECHECK, scenes.PRECISION_FP64):
+                s = dict(base, precision=prec)
+                o = binding.alloc_outputs(W, H, device=f"cuda:{local}")
+                binding.dqj_render(ctx, s, binding.outputs_of(o), stream.cuda_stream)  # warm-up
+                best = 1e30
+                for _ in range(reps):
+                    e0.record(stream)
+                    binding.dqj_render(ctx, s, binding.outputs_of(o), stream.cuda_stream)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    best = min(best, e0.elapsed_time(e1))
+                res[prec] = (o, best, binding.stats_dict(o["stats"]))
+            ref, ref_ms, _ = res[scenes.PRECISION_FP64]
+            rd = ref["depth"][:, :W]
+            rh = torch.isfinite(rd)
+            row = {"frame": name, "fp64_ms": round(ref_ms, 3), "hits_fp64": int(rh.sum())}
+            for prec, tag in ((scenes.PRECISION_FP32, "fp32"), (scenes.PRECISION_FP32_RECHECK, "recheck")):
+                o, ms, st = res[prec]
+                d = o["depth"][:, :W]
+                h = torch.isfinite(d)
+                agree = h == rh
+                both = h & rh
+                err = (d[both].double() - rd[both].double()).abs()
+                row[tag] = {
+                    "ms": round(ms, 3), "speedup_vs_fp64": round(ref_ms / ms, 2),
+                    "flip_frac": float((~agree).sum()) / (W * H),
+                    "iter_mismatch_agreeing": int(((o["iter"][:, :W] != ref["iter"][:, :W]) & agree).sum()),
+                    "depth_err_max": float(err.max()) if err.numel() else 0.0,
+                    "depth_err_median": float(err.median()) if err.numel() else 0.0,
+                }
+                if prec == scenes.PRECISION_FP32_RECHECK:
+                    row[tag]["recheck_rate"] = st["rechecks"] / max(st["samples"], 1)
+                    row[tag]["rechecks"] = st["rechecks"]
+                    row[tag]["fixups"] = st["fixups"]
+            out.append(row)
+    finally:
+        binding.dqj_destroy(ctx)
+    return out
+
+
+def run_precision_only(args, world, rank, local):
+    """C4: precision modes on the 1080p workload frames (one JSON line)."""
+    import torch
+    torch.cuda.set_device(local)
+    from paper_2303_14827_gb300 import binding
+    binding.load()
+    rows = precision_section(local)
+    line = {"metric": "FP32 / FP32+FP64-recheck vs all-FP64: flips, depth error, recheck rate, speedup",
+            "value": statistics.median(r["recheck"]["speedup_vs_fp64"] for r in rows),
+            "unit": "x speedup of FP32+recheck over all-FP64 (median over frames)", "n_gpus": 1,
+            "higher_is_better": True, "data": "synthetic",
+            "config": {"workload": WORKLOAD + "; plus the default c at 1920x1080", "recheck_margin": 1e-3},
+            "frames": rows}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_serve_only(args, world, rank, local):
     """C5: Poisson stream of render requests at offered rates relative to the
     measured saturation throughput (one JSON line)."""
@@ -552,6 +631,8 @@ def main():
     ap.add_argument("--no-serve", action="store_true", help="skip the served/batch sections")
     ap.add_argument("--serve", action="store_true", help="only the Poisson serving benchmark")
     ap.add_argument("--requests", type=int, default=10000)
+    ap.add_argument("--precision-report", action="store_true",
+                    help="only the FP32 / recheck / FP64 comparison on the workload frames")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "dqj":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -560,6 +641,8 @@ def main():
         rc = run_reference(args, world, rank)
     elif args.serve:
         rc = run_serve_only(args, world, rank, local)
+    elif args.precision_report:
+        rc = run_precision_only(args, world, rank, local)
     else:
         rc = run_gpu(args, world, rank, local)
     if world > 1:

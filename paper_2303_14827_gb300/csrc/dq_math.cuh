@@ -194,21 +194,76 @@ __device__ __forceinline__ float2 dq_iter2(const float2 (&zi)[8], float2 (&z)[8]
     return x;
 }
 
+// First step of the paired iteration for a sample of an axis-aligned slice:
+// components 3..7 of the input are zero (the slice origin and basis vanish
+// there), so every product with them is zero and the step reduces to the terms
+// below.  The operations kept are those of dq_iter2 in the same order, so the
+// result is the same (up to the sign of zero components, which no later modulus
+// or comparison sees).  Both squaring modes give the same step here.
+template <int MOD>
+__device__ __forceinline__ float2 dq_iter2_axis_first(const float2 (&zi)[8], float2 (&z)[8], float2 &sp,
+                                                      const PairConsts &P)
+{
+    const float2 r0 = zi[0], r1 = zi[1], r2 = zi[2];
+    const float2 tr0 = f2add(r0, r0);
+    z[0] = f2fma(r0, r0, f2fma(sp, P.neg1, P.c[0]));
+    z[1] = f2fma(tr0, r1, P.c[1]);
+    z[2] = f2fma(tr0, r2, P.c[2]);
+#pragma unroll
+    for (int i = 3; i < 8; ++i) z[i] = P.c[i];
+    sp = f2fma(z[3], z[3], f2fma(z[2], z[2], f2mul(z[1], z[1])));
+    float2 x = f2fma(z[0], z[0], sp);
+    if (MOD == 0) {
+        x = f2fma(z[4], z[4], x);
+        x = f2fma(z[5], z[5], x);
+        x = f2fma(z[6], z[6], x);
+        x = f2fma(z[7], z[7], x);
+    }
+    return x;
+}
+
 // Lockstep classification of two samples per lane (halves .x and .y), same
 // conventions as classify_lockstep.  On entry aa / ab say whether each half has
 // a sample; on return they say whether it stayed bounded (inside), and ca / cb
 // hold the number of steps it stayed bounded (escape count - 1, or max_iter).
-template <int SQ, int MOD, bool RECHECK>
+// AXIS: the samples lie in an axis-aligned slice, only z[0..2] are set on entry
+// (components 3..7 are zero) and the first step takes dq_iter2_axis_first.
+template <int SQ, int MOD, bool RECHECK, bool AXIS = false>
 __device__ __forceinline__ void classify_lockstep2(float2 (&z)[8], const PairConsts &P, float R2, float margin,
                                                    int max_iter, bool &aa, bool &ab, int &ca, int &cb, bool &mga,
                                                    bool &mgb)
 {
     bool ma = false, mb = false;
     int na = 0, nb = 0;
-    float2 sp = dq_sp2(z);
+    float2 sp = AXIS ? f2fma(z[2], z[2], f2mul(z[1], z[1])) : dq_sp2(z);
     float2 w[8];
+    int n0 = 0;
+    if constexpr (AXIS) {  // the first trip, peeled so that its first step takes the axis form
+        n0 = max_iter;
+        float2 x = dq_iter2_axis_first<MOD>(z, w, sp, P);
+        if (RECHECK) {
+            ma = ma || (aa && fabsf(x.x - R2) <= margin);
+            mb = mb || (ab && fabsf(x.y - R2) <= margin);
+        }
+        aa = aa && (x.x <= R2);
+        ab = ab && (x.y <= R2);
+        na += aa ? 1 : 0;
+        nb += ab ? 1 : 0;
+        if (__any_sync(0xffffffffu, aa || ab) && max_iter > 1) {
+            x = dq_iter2<SQ, MOD>(w, z, sp, P);
+            if (RECHECK) {
+                ma = ma || (aa && fabsf(x.x - R2) <= margin);
+                mb = mb || (ab && fabsf(x.y - R2) <= margin);
+            }
+            aa = aa && (x.x <= R2);
+            ab = ab && (x.y <= R2);
+            na += aa ? 1 : 0;
+            nb += ab ? 1 : 0;
+            if (__any_sync(0xffffffffu, aa || ab)) n0 = 2;
+        }
+    }
     // two steps per trip, z -> w -> z, with the escape test after each
-    for (int n = 0; n < max_iter; n += 2) {
+    for (int n = n0; n < max_iter; n += 2) {
         float2 x = dq_iter2<SQ, MOD>(z, w, sp, P);
         if (RECHECK) {
             ma = ma || (aa && fabsf(x.x - R2) <= margin);

@@ -59,7 +59,7 @@ struct alignas(16) FrameDesc {
     uint8_t *rgba;
     int64_t *stats;   // served requests: caller's DQJ_NSTATS counters (device), or NULL
     uint32_t epoch;   // tag for per-pixel dirty flags, changes every frame
-    uint32_t pad;
+    uint32_t axis_slice;  // 1: slice origin and basis are zero in components 3..7
 };
 
 // Counters at the head of the scratch block; zeroed before every frame.

@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(kBlock) march_kernel(const __grid_constant__ F
 // latest outside sample) and the first inside sample kf_*; the iteration and
 // sample counts follow from them once the ray is done.
 // ---------------------------------------------------------------------------
-template <int SQ, int MOD, bool RECHECK>
+template <int SQ, int MOD, bool RECHECK, bool AXIS>
 __global__ void __launch_bounds__(kBlock, 5) march2_kernel(const __grid_constant__ FrameDesc fd, const Scratch sc)
 {
     const int lane = threadIdx.x & 31;
@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(kBlock, 5) march2_kernel(const __grid_constant
         if (lane == 0) tile = atomicAdd(&sc.ctr->tile_next, 1u);
         tile = __shfl_sync(kFull, tile, 0);
         if (tile >= ntiles) break;
-        march2_tile<SQ, MOD, RECHECK>(fd, fd.p2, sc, tile, st);
+        march2_tile<SQ, MOD, RECHECK, AXIS>(fd, fd.p2, sc, tile, st);
     }
     flush_lane_stats<RECHECK>(sc, st, true);
 }
@@ -284,9 +284,12 @@ cudaError_t launch_passes(const FrameDesc &fd, const Scratch &sc, cudaStream_t s
     if (ev) cudaEventRecord(ev[0], st);
     if constexpr (sizeof(T) == 4) {
         if (fd.march_variant == 1) {
-            if (!g_march2) g_march2 = persistent_grid(march2_kernel<SQ, MOD, RECHECK>, num_sms);
+            if (!g_march2) g_march2 = persistent_grid(march2_kernel<SQ, MOD, RECHECK, false>, num_sms);
             const int gm = (int)min((unsigned)g_march2, (ntiles + 3u) / 4u);
-            march2_kernel<SQ, MOD, RECHECK><<<gm > 0 ? gm : 1, kBlock, 0, st>>>(fd, sc);
+            if (fd.axis_slice)
+                march2_kernel<SQ, MOD, RECHECK, true><<<gm > 0 ? gm : 1, kBlock, 0, st>>>(fd, sc);
+            else
+                march2_kernel<SQ, MOD, RECHECK, false><<<gm > 0 ? gm : 1, kBlock, 0, st>>>(fd, sc);
         }
     }
     if (sizeof(T) != 4 || fd.march_variant != 1) {

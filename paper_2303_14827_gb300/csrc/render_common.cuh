@@ -198,7 +198,7 @@ __device__ __forceinline__ void shade_write(const FrameDesc &fd, const FrameT<T>
 }
 
 // One 64-ray tile of the paired march (see march2_kernel); all 32 lanes call.
-template <int SQ, int MOD, bool RECHECK>
+template <int SQ, int MOD, bool RECHECK, bool AXIS = false>
 __device__ __forceinline__ void march2_tile(const FrameDesc &fd, const PairConsts &P, const Scratch &sc, unsigned tile,
                                             LaneStats &st)
 {
@@ -235,10 +235,10 @@ __device__ __forceinline__ void march2_tile(const FrameDesc &fd, const PairConst
         kf = f2add(kf, make_float2(1.f, 1.f));
         float2 z[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) z[i] = f2fma(t, D[i], P.A[i]);
+        for (int i = 0; i < (AXIS ? 3 : 8); ++i) z[i] = f2fma(t, D[i], P.A[i]);  // AXIS: the rest are 0
         bool ina = acta, inb = actb, mga, mgb;
         int ca, cb;
-        classify_lockstep2<SQ, MOD, RECHECK>(z, P, F.R2, F.margin, max_iter, ina, inb, ca, cb, mga, mgb);
+        classify_lockstep2<SQ, MOD, RECHECK, AXIS>(z, P, F.R2, F.margin, max_iter, ina, inb, ca, cb, mga, mgb);
         if (RECHECK) {
             const bool pa = acta && mga, pb = actb && mgb;
             if (warp_push(pa, make_int4(ya * fd.W + xa, k | (kMarchSample << 16), 0, ina ? 0 : ca + 1), sc.queue,

@@ -104,6 +104,12 @@ void derive_frame(const dqj_params &p, FrameDesc &fd, int tile_w, int tile_h)
         F.A[i] = p.slice_origin[i] + p.eye[0] * p.slice_basis[0][i] + p.eye[1] * p.slice_basis[1][i] +
                  p.eye[2] * p.slice_basis[2][i];
     }
+    // a slice through the first three components only: zeta_0 is zero in 3..7
+    fd.axis_slice = 1;
+    for (int i = 3; i < 8; ++i)
+        if (p.slice_origin[i] != 0.0 || p.slice_basis[0][i] != 0.0 || p.slice_basis[1][i] != 0.0 ||
+            p.slice_basis[2][i] != 0.0)
+            fd.axis_slice = 0;
     double f[3], r[3], u[3];
     for (int a = 0; a < 3; ++a) f[a] = p.target[a] - p.eye[a];
     double fl = std::sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
