@@ -183,7 +183,10 @@ __global__ void __launch_bounds__(kBlock, 4) serve_kernel(ServeCtl ctl)
         LaneStats st;
         if (kind == 1) {
             PairConsts P = fd.p2;
-            march2_tile<0, 0, false>(fd, P, sc, item, st);
+            if (fd.axis_slice)
+                march2_tile<0, 0, false, true>(fd, P, sc, item, st);
+            else
+                march2_tile<0, 0, false, false>(fd, P, sc, item, st);
             flush_lane_stats<false>(sc, st, true);
             __threadfence();
             unsigned long long done = 0;
