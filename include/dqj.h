@@ -113,6 +113,8 @@ typedef struct {
                                    marks a sample for FP64 re-evaluation; 0..0.5      */
     int32_t square_mode;        /* DQJ_SQUARE_*                                       */
     int32_t modulus_mode;       /* DQJ_MODULUS_*                                      */
+    double k_specular;          /* Eq. phong specular coefficient k_s >= 0 (0: off)   */
+    double shininess;           /* Eq. phong specular exponent s, 0..10000            */
 } dqj_params;
 
 /*

@@ -73,6 +73,8 @@ class Scene(ctypes.Structure):
         ("albedo", ctypes.c_double * 3),
         ("square_mode", ctypes.c_int32),
         ("modulus_mode", ctypes.c_int32),
+        ("k_specular", ctypes.c_double),
+        ("shininess", ctypes.c_double),
     ]
 
 
@@ -242,6 +244,8 @@ def make_scene(p: dict) -> Scene:
     s.albedo[:] = [float(x) for x in p["albedo"]]
     s.square_mode = int(p.get("square_mode", 0))
     s.modulus_mode = int(p.get("modulus_mode", 0))
+    s.k_specular = float(p.get("k_specular", 0.0))
+    s.shininess = float(p.get("shininess", 32.0))
     return s
 
 

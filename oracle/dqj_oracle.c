@@ -72,6 +72,8 @@ typedef struct {
     double albedo[3];
     int32_t square_mode;  /* 0 ALGEBRAIC, 1 PAPER_COMPONENTWISE */
     int32_t modulus_mode; /* 0 EUCLID8, 1 DUALNUM */
+    double k_specular;    /* Eq. phong k_s (0: no specular term) */
+    double shininess;     /* Eq. phong exponent s */
 } or_scene;
 
 /* Per-pixel trace, for tests that check the march and bisection logic. */
@@ -494,12 +496,22 @@ static void render_pixel(const or_scene *s, int i, int j, pixel_out *po, or_trac
         po->normal[2] = g[2] / gl;
     }
 
-    /* Shading, Eq. phong with the ambient and diffuse terms. */
+    /* Shading, Eq. phong: ambient, diffuse and (when k_s > 0) specular terms
+     * with unit light intensities.  The specular term uses the reflected light
+     * r = 2 n (n.l) - l and the unit vector to the eye v = -d, and counts only
+     * when the light is in front (n.l > 0) and r.v > 0. */
     double l[3] = {s->light_dir[0], s->light_dir[1], s->light_dir[2]};
     v3_normalize(l);
     double ndl = v3_dot(po->normal, l);
+    double spec = 0.0;
+    if (s->k_specular > 0.0 && ndl > 0.0) {
+        double r[3], rv = 0.0;
+        for (int a = 0; a < 3; ++a) r[a] = 2.0 * ndl * po->normal[a] - l[a];
+        for (int a = 0; a < 3; ++a) rv -= r[a] * t.d[a];
+        if (rv > 0.0) spec = s->k_specular * pow(rv, s->shininess);
+    }
     if (ndl < 0.0) ndl = 0.0;
-    double v = s->k_ambient + s->k_diffuse * ndl;
+    double v = s->k_ambient + s->k_diffuse * ndl + spec;
     if (v < 0.0) v = 0.0;
     if (v > 1.0) v = 1.0;
     po->rgba[0] = to_u8(v * s->albedo[0]);

@@ -70,6 +70,8 @@ class dqj_params(ctypes.Structure):
         ("recheck_margin", ctypes.c_double),
         ("square_mode", ctypes.c_int32),
         ("modulus_mode", ctypes.c_int32),
+        ("k_specular", ctypes.c_double),
+        ("shininess", ctypes.c_double),
     ]
 
 
@@ -159,6 +161,8 @@ def make_params(scene: dict) -> dqj_params:
         getattr(p, k)[:] = [float(x) for x in scene[k]]
     for k in ("fov_y_deg", "escape_radius", "normal_h", "k_ambient", "k_diffuse", "recheck_margin"):
         setattr(p, k, float(scene[k]))
+    p.k_specular = float(scene.get("k_specular", 0.0))
+    p.shininess = float(scene.get("shininess", 32.0))
     for k in ("width", "height", "max_iter", "march_steps", "bisect_steps", "precision", "square_mode",
               "modulus_mode"):
         setattr(p, k, int(scene[k]))

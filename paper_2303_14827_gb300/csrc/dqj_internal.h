@@ -29,6 +29,7 @@ struct FrameT {
     T h;           // normal step
     T light[3];    // unit vector to the light
     T ka, kd, albedo[3];
+    T ks, shin;  // Eq. phong specular coefficient and exponent (ks = 0: off)
 };
 
 // Encoding of a queued FP64 recheck: which sample of which pixel.

@@ -181,8 +181,14 @@ __device__ __forceinline__ void shade_write(const FrameDesc &fd, const FrameT<T>
         n[2] = g2 / gl;
     }
     T ndl = n[0] * F.light[0] + n[1] * F.light[1] + n[2] * F.light[2];
+    T spec = T(0);
+    if (F.ks > T(0) && ndl > T(0)) {  // reflected light r = 2n(n.l) - l against v = -d
+        const T rv = -((T(2) * ndl * n[0] - F.light[0]) * d[0] + (T(2) * ndl * n[1] - F.light[1]) * d[1] +
+                       (T(2) * ndl * n[2] - F.light[2]) * d[2]);
+        if (rv > T(0)) spec = F.ks * pow(rv, F.shin);
+    }
     ndl = ndl > T(0) ? ndl : T(0);
-    T v = F.ka + F.kd * ndl;
+    T v = F.ka + F.kd * ndl + spec;
     v = v < T(0) ? T(0) : (v > T(1) ? T(1) : v);
     const int64_t o = (int64_t)y * fd.pitch + x;
     if (fd.iter) fd.iter[o] = iter;

@@ -79,6 +79,9 @@ dqj_status validate(const dqj_params *p)
         return fail(DQJ_ERR_INVALID, "light_dir must be non-zero");
     if (!std::isfinite(p->k_ambient) || !std::isfinite(p->k_diffuse))
         return fail(DQJ_ERR_INVALID, "k_ambient and k_diffuse must be finite");
+    if (!(p->k_specular >= 0.0 && p->k_specular <= 1e6))
+        return fail(DQJ_ERR_INVALID, "k_specular must be finite and >= 0");
+    if (!(p->shininess >= 0.0 && p->shininess <= 1e4)) return fail(DQJ_ERR_INVALID, "shininess must be in [0, 10000]");
     for (int a = 0; a < 3; ++a)
         if (!(p->albedo[a] >= 0.0 && p->albedo[a] <= 1.0)) return fail(DQJ_ERR_INVALID, "albedo must be in [0, 1]");
     return DQJ_OK;
@@ -145,6 +148,8 @@ void derive_frame(const dqj_params &p, FrameDesc &fd, int tile_w, int tile_h)
     for (int a = 0; a < 3; ++a) F.light[a] = p.light_dir[a] / ll;
     F.ka = p.k_ambient;
     F.kd = p.k_diffuse;
+    F.ks = p.k_specular;
+    F.shin = p.shininess;
     cast_frame<float>(F, fd.f);
     for (int i = 0; i < 8; ++i) {
         fd.p2.c[i] = make_float2(fd.f.c[i], fd.f.c[i]);
@@ -354,6 +359,8 @@ dqj_status dqj_default_params(dqj_params *p)
     p->recheck_margin = 1e-3;
     p->square_mode = DQJ_SQUARE_ALGEBRAIC;
     p->modulus_mode = DQJ_MODULUS_EUCLID8;
+    p->k_specular = 0.0;
+    p->shininess = 32.0;
     return DQJ_OK;
 }
 

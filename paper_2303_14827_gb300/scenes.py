@@ -83,6 +83,8 @@ def default_scene(**overrides) -> dict:
         "recheck_margin": 1e-3,
         "square_mode": SQUARE_ALGEBRAIC,
         "modulus_mode": MODULUS_EUCLID8,
+        "k_specular": 0.0,
+        "shininess": 32.0,
     }
     for k, v in overrides.items():
         if k not in s:

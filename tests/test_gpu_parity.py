@@ -117,6 +117,7 @@ def test_pitch_and_partial_planes(rdr):
     dict(square_mode=scenes.SQUARE_PAPER_COMPONENTWISE),
     dict(modulus_mode=scenes.MODULUS_DUALNUM),
     dict(square_mode=1, modulus_mode=1),
+    dict(k_specular=0.5, shininess=16.0, light_dir=[0.3, 0.4, 1.0]),  # Eq. phong specular term
 ])
 def test_edge_cases(rdr, over):
     s = scenes.default_scene(width=64, height=48, **over)

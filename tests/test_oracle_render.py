@@ -274,3 +274,39 @@ def test_normal_overflow_guard_c0():
                 assert float(np.dot(nrm, g / np.linalg.norm(g))) > 1.0 - 1e-9
                 n_grad += 1
     assert n_guard > 10 and n_grad > 10, (n_guard, n_grad)
+
+
+def test_c0_ball_specular_closed_form():
+    # Eq. phong with the specular term on the c = 0 ball: the expected shade from
+    # the closed-form central-difference normal, the reflected light
+    # r = 2n(n.l) - l and the unit vector to the eye v = -d.
+    W = H = 40
+    ks, sh = 0.6, 20.0
+    s = scenes.default_scene(c=[0.0] * 8, width=W, height=H, fov_y_deg=60.0, k_specular=ks, shininess=sh,
+                             light_dir=[0.3, 0.4, 1.0])
+    mi = s["max_iter"]
+    out = oracle.render(s)
+    l = np.array(s["light_dir"]) / np.linalg.norm(s["light_dir"])
+    n_hit = n_lit = 0
+    for j in range(H):
+        for i in range(W):
+            depth = out["depth"][j, i]
+            if not math.isfinite(depth):
+                continue
+            o, d = oracle.camera_ray(s, i, j)
+            p = o + depth * d
+            h, e = s["normal_h"], 2.0 ** (mi + 1)
+            g = np.array([np.linalg.norm(p + h * ax) ** e - np.linalg.norm(p - h * ax) ** e for ax in np.eye(3)])
+            n = g / np.linalg.norm(g)
+            ndl = float(np.dot(n, l))
+            spec = 0.0
+            if ndl > 0:
+                r = 2.0 * ndl * n - l
+                rv = -float(np.dot(r, d))
+                if rv > 0:
+                    spec = ks * rv ** sh
+            v = min(1.0, 0.15 + 0.85 * max(0.0, ndl) + spec)
+            assert abs(int(out["rgba"][j, i, 0]) - math.floor(255 * v + 0.5)) <= 1
+            n_hit += 1
+            n_lit += spec * 255 > 10
+    assert n_hit > 50 and n_lit > 5  # the highlight is on the visible cap
