@@ -597,6 +597,61 @@ def run_precision_only(args, world, rank, local):
     return 0
 
 
+def sweep_section(local, reps=3):
+    """Level of detail against cost (the paper's Fig. detail): sample points N
+    and iteration limit n swept on two 1920x1080 scenes with visible sets (the
+    default c and the Fig. highres2 constant), FP32: ms per frame (best of
+    reps), DQ iterations/s and the fraction of hit pixels."""
+    import torch
+
+    from paper_2303_14827_gb300 import binding, scenes
+    bases = {"default_c": scenes.default_scene(width=1920, height=1080, bisect_steps=10),
+             "highres2": scenes.default_scene(c=list(scenes.PAPER_C_VALUES["highres2"]), width=1920, height=1080,
+                                              bisect_steps=10)}
+    ctx = binding.dqj_create(local)
+    stream = torch.cuda.current_stream(local)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    o = binding.alloc_outputs(1920, 1080, device=f"cuda:{local}")
+    rows = []
+    try:
+        for name, base in bases.items():
+            for n_steps in (128, 256, 512, 1024):
+                for mi in (6, 10, 15, 24):
+                    sc = dict(base, march_steps=n_steps, max_iter=mi)
+                    binding.dqj_render(ctx, sc, binding.outputs_of(o), stream.cuda_stream)
+                    best = 1e30
+                    for _ in range(reps):
+                        e0.record(stream)
+                        binding.dqj_render(ctx, sc, binding.outputs_of(o), stream.cuda_stream)
+                        e1.record(stream)
+                        torch.cuda.synchronize()
+                        best = min(best, e0.elapsed_time(e1))
+                    st = binding.stats_dict(o["stats"])
+                    it = st["class_iters"] + st["normal_iters"]
+                    rows.append({"scene": name, "march_steps": n_steps, "max_iter": mi, "ms": round(best, 3),
+                                 "iters_per_s": it / (best * 1e-3), "hit_frac": st["hits"] / (1920 * 1080)})
+    finally:
+        binding.dqj_destroy(ctx)
+    return rows
+
+
+def run_sweep_only(args, world, rank, local):
+    import torch
+    torch.cuda.set_device(local)
+    from paper_2303_14827_gb300 import binding
+    binding.load()
+    rows = sweep_section(local)
+    line = {"metric": "level of detail vs cost: ms per 1080p frame over march steps x max_iter",
+            "value": statistics.median(r["iters_per_s"] for r in rows), "unit": "DQ iterations/s (median)",
+            "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+            "config": {"workload": "1920x1080, default c and Fig. highres2 c, N in {128,256,512,1024}, "
+                                   "max_iter in {6,10,15,24}, 10 bisect, FP32"},
+            "rows": rows}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_serve_only(args, world, rank, local):
     """C5: Poisson stream of render requests at offered rates relative to the
     measured saturation throughput (one JSON line)."""
@@ -631,6 +686,7 @@ def main():
     ap.add_argument("--no-serve", action="store_true", help="skip the served/batch sections")
     ap.add_argument("--serve", action="store_true", help="only the Poisson serving benchmark")
     ap.add_argument("--requests", type=int, default=10000)
+    ap.add_argument("--sweep", action="store_true", help="only the march steps x max_iter detail sweep")
     ap.add_argument("--precision-report", action="store_true",
                     help="only the FP32 / recheck / FP64 comparison on the workload frames")
     args = ap.parse_args()
@@ -643,6 +699,8 @@ def main():
         rc = run_serve_only(args, world, rank, local)
     elif args.precision_report:
         rc = run_precision_only(args, world, rank, local)
+    elif args.sweep:
+        rc = run_sweep_only(args, world, rank, local)
     else:
         rc = run_gpu(args, world, rank, local)
     if world > 1:

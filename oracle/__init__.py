@@ -135,6 +135,10 @@ def lib():
             L.or_render.argtypes = [ctypes.POINTER(Scene), _I64, ctypes.c_int64, ctypes.c_int,
                                     _I32, _D, _D, _U8, _I64, _I64, _I64]
             L.or_render.restype = ctypes.c_int
+            L.or_voxel_center.argtypes = [ctypes.POINTER(Scene), ctypes.c_int32, ctypes.c_int64, _D]
+            L.or_voxelize.argtypes = [ctypes.POINTER(Scene), ctypes.c_int32, _I64, ctypes.c_int64, ctypes.c_int,
+                                      _U8, _I32, _I64]
+            L.or_voxelize.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -326,3 +330,30 @@ def render(p: dict, pixels=None, threads: int = 0, want_pixel_iters: bool = Fals
     if piters is not None:
         out["pixel_iters"] = piters.reshape(shape)
     return out
+
+
+def voxel_center(p: dict, g: int, lin: int) -> np.ndarray:
+    """Scene-space centre of linear voxel cell `lin` of the g^3 grid over the box."""
+    out = np.zeros(3)
+    lib().or_voxel_center(ctypes.byref(make_scene(p)), int(g), int(lin), _dp(out))
+    return out
+
+
+def voxelize(p: dict, g: int, cells=None, threads: int = 0) -> dict:
+    """Voxel occupancy grid (Fig. voxels) in FP64: occupancy u8 (1 inside) and
+    escape count int32 (0 inside) per cell.  Whole grids come back shaped
+    [g, g, g] indexed [k, j, i] (x fastest); cell lists come back flat."""
+    s = make_scene(p)
+    if cells is None:
+        n, shape, arr = g ** 3, (g, g, g), None
+    else:
+        arr = np.ascontiguousarray(np.asarray(cells, dtype=np.int64).reshape(-1))
+        n, shape = arr.size, (arr.size,)
+    occ = np.zeros(n, np.uint8)
+    cnt = np.zeros(n, np.int32)
+    it = ctypes.c_int64(0)
+    used = lib().or_voxelize(ctypes.byref(s), int(g), arr.ctypes.data_as(_I64) if arr is not None else None,
+                             ctypes.c_int64(n), int(threads), occ.ctypes.data_as(_U8), cnt.ctypes.data_as(_I32),
+                             ctypes.byref(it))
+    return {"occupancy": occ.reshape(shape), "count": cnt.reshape(shape), "iters": int(it.value),
+            "threads": int(used)}
