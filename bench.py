@@ -635,6 +635,61 @@ def sweep_section(local, reps=3):
     return rows
 
 
+def voxel_section(local, reps=5):
+    """Voxel occupancy grids (the paper's Fig. voxels prototype) of the default c:
+    the paper's 50^3 and 100^3 and the largest 1024^3, FP32 (and FP32+recheck at
+    1024^3): ms per grid (best of reps), cells/s, DQ iterations/s and the
+    fraction of the FP32 FMA peak."""
+    import torch
+
+    from paper_2303_14827_gb300 import binding, scenes
+    ctx = binding.dqj_create(local)
+    stream = torch.cuda.current_stream(local)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    num_sms = torch.cuda.get_device_properties(local).multi_processor_count
+    peak = num_sms * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6
+    rows = []
+    try:
+        for g, prec in ((50, 0), (100, 0), (1024, 0), (1024, 1)):
+            s = scenes.default_scene(max_iter=16, precision=prec)
+            occ = torch.empty(g ** 3, dtype=torch.uint8, device=f"cuda:{local}")
+            st = torch.zeros(binding.DQJ_NSTATS, dtype=torch.int64, device=f"cuda:{local}")
+            binding.dqj_voxelize(ctx, s, g, occ, None, st, stream.cuda_stream)
+            best = 1e30
+            for _ in range(reps):
+                e0.record(stream)
+                binding.dqj_voxelize(ctx, s, g, occ, None, st, stream.cuda_stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+            sd = binding.stats_dict(st)
+            rate = sd["class_iters"] / (best * 1e-3)
+            rows.append({"grid": g, "precision": prec, "ms": round(best, 4), "cells_per_s": g ** 3 / (best * 1e-3),
+                         "iters_per_s": rate, "frac_fp32_peak": round(rate * FLOPS_PER_ITER / peak, 4),
+                         "inside_frac": sd["hits"] / g ** 3, "rechecks": sd["rechecks"], "fixups": sd["fixups"]})
+            del occ
+    finally:
+        binding.dqj_destroy(ctx)
+    return rows
+
+
+def run_voxel_only(args, world, rank, local):
+    import torch
+    torch.cuda.set_device(local)
+    from paper_2303_14827_gb300 import binding
+    binding.load()
+    rows = voxel_section(local)
+    big = next(r for r in rows if r["grid"] == 1024 and r["precision"] == 0)
+    line = {"metric": "voxel occupancy grid: cells/s and DQ iterations/s (fraction of FP32 FMA peak)",
+            "value": big["iters_per_s"], "unit": "DQ iterations/s (1024^3, FP32)", "n_gpus": 1,
+            "higher_is_better": True, "data": "synthetic",
+            "config": {"workload": "default c, default slice, max_iter 16, grids 50^3 / 100^3 / 1024^3 over the box"},
+            "rows": rows}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_sweep_only(args, world, rank, local):
     import torch
     torch.cuda.set_device(local)
@@ -687,6 +742,7 @@ def main():
     ap.add_argument("--serve", action="store_true", help="only the Poisson serving benchmark")
     ap.add_argument("--requests", type=int, default=10000)
     ap.add_argument("--sweep", action="store_true", help="only the march steps x max_iter detail sweep")
+    ap.add_argument("--voxel", action="store_true", help="only the voxel occupancy grid benchmark")
     ap.add_argument("--precision-report", action="store_true",
                     help="only the FP32 / recheck / FP64 comparison on the workload frames")
     args = ap.parse_args()
@@ -701,6 +757,8 @@ def main():
         rc = run_precision_only(args, world, rank, local)
     elif args.sweep:
         rc = run_sweep_only(args, world, rank, local)
+    elif args.voxel:
+        rc = run_voxel_only(args, world, rank, local)
     else:
         rc = run_gpu(args, world, rank, local)
     if world > 1:

@@ -238,6 +238,37 @@ dqj_status dqj_tile_shape(dqj_ctx *ctx, const dqj_params *p, int32_t *variant, i
 dqj_status dqj_set_profiling(dqj_ctx *ctx, int32_t ring_frames);
 dqj_status dqj_pass_ms(dqj_ctx *ctx, int32_t frames, float *ms);
 
+/*
+ * dqj_voxelize -- voxel occupancy grid (Fig. voxels: the paper's voxel
+ * prototype, which the paper compares with the ray-traced image).
+ *
+ * Classifies the centre of every cell of a grid_n^3 grid over the march box
+ * [box_min, box_max] like a ray sample: cell (i, j, k) has centre
+ * box_min + (idx + 1/2) (box_max - box_min) / grid_n per axis, is mapped into
+ * the slice (slice_origin, slice_basis) and iterated (c, max_iter,
+ * escape_radius, square_mode, modulus_mode, precision; recheck_margin for
+ * DQJ_FP32_RECHECK).  The camera, image size, march, normal and shading fields
+ * of p are validated but unused.
+ *
+ * Outputs (caller-owned device memory, linear index (k grid_n + j) grid_n + i,
+ * x fastest; either may be NULL but not both):
+ *   occupancy  uint8[grid_n^3]: 1 when the centre stays bounded for max_iter
+ *              steps (inside), else 0;
+ *   counts     uint16[grid_n^3], 2-byte aligned: escape count 1..max_iter, 0 inside;
+ *   stats      int64[DQJ_NSTATS] or NULL: [CLASS_ITERS] DQ iterations of the
+ *              classification, [SAMPLES] cells, [HITS] inside cells of the
+ *              final grid, [RECHECKS] cells re-classified in FP64, [FIXUPS]
+ *              cells the FP64 pass changed, [FIXUP_ITERS] its iterations,
+ *              [OVERFLOW] recheck-queue overflows (the whole grid is then
+ *              re-classified in FP64).
+ * Stream-ordered on cuda_stream like dqj_render, and ordered with the
+ * context's renders.  Errors: DQJ_ERR_INVALID for a bad p, grid_n outside
+ * 1..DQJ_VOXEL_MAX_GRID, misaligned or both-NULL outputs, or a mock context.
+ */
+#define DQJ_VOXEL_MAX_GRID 1024
+dqj_status dqj_voxelize(dqj_ctx *ctx, const dqj_params *p, int32_t grid_n, uint8_t *occupancy, uint16_t *counts,
+                        int64_t *stats, void *cuda_stream);
+
 /* Largest width * height dqj_render_noalloc accepts (e.g. 512 x 512). */
 #define DQJ_NOALLOC_MAX_PIXELS 262144u
 

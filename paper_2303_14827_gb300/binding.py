@@ -130,6 +130,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         L.dqj_set_profiling.argtypes = [ctypes.c_void_p, ctypes.c_int32]
         L.dqj_pass_ms.argtypes = [ctypes.c_void_p, ctypes.c_int32, P(ctypes.c_float)]
         L.dqj_serve_stats.argtypes = [ctypes.c_void_p, P(ctypes.c_int64)]
+        L.dqj_voxelize.argtypes = [ctypes.c_void_p, P(dqj_params), ctypes.c_int32, ctypes.c_void_p,
+                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
         for name in declared_symbols():
             fn = getattr(L, name)
             if name != "dqj_last_error":
@@ -210,7 +212,9 @@ def dqj_destroy(ctx: int) -> None:
 
 
 def _ptr(t):
-    return None if t is None else t.data_ptr()
+    if t is None or isinstance(t, int):
+        return t
+    return t.data_ptr()
 
 
 def make_outputs(iter=None, depth=None, normal=None, rgba=None, pitch_px: int = 0, stats=None) -> dqj_outputs:
@@ -230,6 +234,7 @@ def dqj_render_host(ctx: int, scene: dict, outputs: dqj_outputs) -> None:
 
 
 DQJ_NOALLOC_MAX_PIXELS = 262144
+DQJ_VOXEL_MAX_GRID = 1024
 
 
 def dqj_render_noalloc(scene: dict, outputs: dqj_outputs, stream: int = 0) -> None:
@@ -278,6 +283,16 @@ def dqj_pass_ms(ctx: int, frames: int) -> list:
     ms = (ctypes.c_float * (4 * frames))()
     check(load().dqj_pass_ms(ctypes.c_void_p(ctx), int(frames), ms))
     return [list(ms[4 * i:4 * i + 4]) for i in range(frames)]
+
+
+def dqj_voxelize(ctx: int, scene: dict, grid_n: int, occupancy=None, counts=None, stats=None,
+                 stream: int = 0) -> None:
+    """Voxel occupancy grid into caller-owned device buffers (torch tensors or
+    raw pointers): occupancy uint8[g^3], counts uint16 (int16 tensor) [g^3],
+    stats int64[DQJ_NSTATS]."""
+    p = make_params(scene)
+    check(load().dqj_voxelize(ctypes.c_void_p(ctx), ctypes.byref(p), int(grid_n), _ptr(occupancy), _ptr(counts),
+                              _ptr(stats), ctypes.c_void_p(stream)))
 
 
 SERVE_STAT_NAMES = ("launches", "restarts", "packed", "plain", "batches", "admit_ns", "completed", "loops")

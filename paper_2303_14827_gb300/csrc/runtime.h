@@ -59,6 +59,9 @@ struct dqj_ctx {
     std::map<int, std::pair<int, int>> tiles;
     std::mutex tiles_mu;             // guards tiles (read by the serving thread too)
     dqj::ServeState *serve = nullptr;
+    // dqj_voxelize scratch: counter block + FP64 recheck queue; grow-only
+    void *vox_scratch = nullptr;
+    size_t vox_bytes = 0;
     // profiling ring: ring_frames x 5 events, next slot, renders recorded
     std::vector<cudaEvent_t> ev;
     int ring_frames = 0;

@@ -720,6 +720,7 @@ dqj_status dqj_destroy(dqj_ctx *ctx)
         if (ctx->host_stream) cudaStreamSynchronize(ctx->host_stream);
         scratch_free(ctx->scratch);
         if (ctx->host_planes) cudaFree(ctx->host_planes);
+        if (ctx->vox_scratch) cudaFree(ctx->vox_scratch);
         if (ctx->host_stream) cudaStreamDestroy(ctx->host_stream);
         if (ctx->done_ev) cudaEventDestroy(ctx->done_ev);
         for (auto &v : ctx->ev)

@@ -71,3 +71,26 @@ def test_null_arguments_are_errors_not_crashes(lib):
 def test_serve_stats_layout_matches_header():
     text = open(binding.HEADER).read()
     assert re.search(r"#define DQJ_NSERVE_STATS (\d+)", text).group(1) == str(len(binding.SERVE_STAT_NAMES))
+
+
+def test_voxelize_validation_on_a_mock_context(monkeypatch):
+    ctx = binding.dqj_create(-1)
+    try:
+        s = scenes.default_scene()
+        for g in (0, binding.DQJ_VOXEL_MAX_GRID + 1):
+            with pytest.raises(binding.DqjError) as ei:
+                binding.dqj_voxelize(ctx, s, g, 4096, 8192)
+            assert ei.value.status == binding.DQJ_ERR_INVALID and "grid_n" in binding.last_error()
+        with pytest.raises(binding.DqjError) as ei:
+            binding.dqj_voxelize(ctx, s, 8, None, None)
+        assert "both NULL" in binding.last_error()
+        with pytest.raises(binding.DqjError) as ei:
+            binding.dqj_voxelize(ctx, s, 8, 4096, 8193)
+        assert "aligned" in binding.last_error()
+        with pytest.raises(binding.DqjError) as ei:
+            binding.dqj_voxelize(ctx, s, 8, 4096, 8192)
+        assert "mock" in binding.last_error()
+    finally:
+        binding.dqj_destroy(ctx)
+    text = open(binding.HEADER).read()
+    assert re.search(r"#define DQJ_VOXEL_MAX_GRID (\d+)", text).group(1) == str(binding.DQJ_VOXEL_MAX_GRID)
