@@ -75,6 +75,11 @@ class Scene(ctypes.Structure):
         ("modulus_mode", ctypes.c_int32),
         ("k_specular", ctypes.c_double),
         ("shininess", ctypes.c_double),
+        ("traversal", ctypes.c_int32),
+        ("de_max_steps", ctypes.c_int32),
+        ("de_epsilon", ctypes.c_double),
+        ("de_step_scale", ctypes.c_double),
+        ("de_bound_radius", ctypes.c_double),
     ]
 
 
@@ -96,6 +101,8 @@ class Trace(ctypes.Structure):
         ("d", ctypes.c_double * 3),
         ("class_iters", ctypes.c_int64),
         ("normal_iters", ctypes.c_int64),
+        ("de_steps", ctypes.c_int32),
+        ("pad2", ctypes.c_int32),
     ]
 
 
@@ -135,6 +142,8 @@ def lib():
             L.or_render.argtypes = [ctypes.POINTER(Scene), _I64, ctypes.c_int64, ctypes.c_int,
                                     _I32, _D, _D, _U8, _I64, _I64, _I64]
             L.or_render.restype = ctypes.c_int
+            L.or_de_distance.argtypes = [ctypes.POINTER(Scene), _D, _D, _I64]
+            L.or_de_distance.restype = ctypes.c_int
             L.or_voxel_center.argtypes = [ctypes.POINTER(Scene), ctypes.c_int32, ctypes.c_int64, _D]
             L.or_voxelize.argtypes = [ctypes.POINTER(Scene), ctypes.c_int32, _I64, ctypes.c_int64, ctypes.c_int,
                                       _U8, _I32, _I64]
@@ -250,6 +259,11 @@ def make_scene(p: dict) -> Scene:
     s.modulus_mode = int(p.get("modulus_mode", 0))
     s.k_specular = float(p.get("k_specular", 0.0))
     s.shininess = float(p.get("shininess", 32.0))
+    s.traversal = int(p.get("traversal", 0))
+    s.de_max_steps = int(p.get("de_max_steps", 512))
+    s.de_epsilon = float(p.get("de_epsilon", 1e-3))
+    s.de_step_scale = float(p.get("de_step_scale", 1.0))
+    s.de_bound_radius = float(p.get("de_bound_radius", 0.0))
     return s
 
 
@@ -279,7 +293,7 @@ def trace_pixel(p: dict, i: int, j: int) -> dict:
     s = make_scene(p)
     t = Trace()
     lib().or_trace_pixel(ctypes.byref(s), int(i), int(j), ctypes.byref(t))
-    out = {name: getattr(t, name) for name, _ in Trace._fields_ if name not in ("o", "d", "pad")}
+    out = {name: getattr(t, name) for name, _ in Trace._fields_ if name not in ("o", "d", "pad", "pad2")}
     out["o"] = np.array(t.o[:])
     out["d"] = np.array(t.d[:])
     return out
@@ -357,3 +371,13 @@ def voxelize(p: dict, g: int, cells=None, threads: int = 0) -> dict:
                              ctypes.byref(it))
     return {"occupancy": occ.reshape(shape), "count": cnt.reshape(shape), "iters": int(it.value),
             "threads": int(used)}
+
+
+def de_distance(p: dict, point) -> tuple:
+    """Distance estimate (Eq. distfract2) at a scene point: (escape count or 0
+    when inside, estimate, DQ iterations)."""
+    d = ctypes.c_double(0.0)
+    it = ctypes.c_int64(0)
+    pt = np.ascontiguousarray(np.asarray(point, dtype=np.float64))
+    n = lib().or_de_distance(ctypes.byref(make_scene(p)), _dp(pt), ctypes.byref(d), ctypes.byref(it))
+    return int(n), float(d.value), int(it.value)

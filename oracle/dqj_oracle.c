@@ -74,6 +74,11 @@ typedef struct {
     int32_t modulus_mode; /* 0 EUCLID8, 1 DUALNUM */
     double k_specular;    /* Eq. phong k_s (0: no specular term) */
     double shininess;     /* Eq. phong exponent s */
+    int32_t traversal;    /* 0 fixed-step march + bisection, 1 distance-estimate sphere tracing */
+    int32_t de_max_steps; /* DE: step limit per ray */
+    double de_epsilon;    /* DE: a sample whose estimate is below this is a hit */
+    double de_step_scale; /* DE: step = scale * estimate */
+    double de_bound_radius; /* DE: bounding sphere about the origin (0: box only) */
 } or_scene;
 
 /* Per-pixel trace, for tests that check the march and bisection logic. */
@@ -89,6 +94,8 @@ typedef struct {
     double o[3], d[3];
     int64_t class_iters;  /* DQ iterations with escape test (march + bisection) */
     int64_t normal_iters; /* DQ iterations of the six normal evaluations        */
+    int32_t de_steps;     /* DE: samples taken                                  */
+    int32_t pad2;
 } or_trace;
 
 /* ------------------------------------------------------------------------- */
@@ -397,6 +404,74 @@ static uint8_t to_u8(double v)
     return (uint8_t)x;
 }
 
+/*
+ * Distance estimate at a scene point p (Method, "Ray-Marching", Eq. distfract2,
+ * with the derivative recurrence of Eq. distfract read as
+ * |zeta'_{n+1}| = 2 |zeta_n| |zeta'_n|, |zeta'_0| = 1).  Iterates from the slice
+ * image of p until the modulus exceeds R^2 at step n, and returns n with
+ * *dist = 0.5 |zeta_n| / |zeta'_n| ln |zeta_n|, |zeta| = sqrt(modulus).  Returns 0
+ * (inside, *dist = 0) when no escape happens within max_iter steps.
+ */
+int or_de_distance(const or_scene *s, const double *p, double *dist, int64_t *iters)
+{
+    double z[8], sq[8];
+    double r2 = s->escape_radius * s->escape_radius;
+    double dr = 1.0;
+    or_slice_point(s, p, z);
+    for (int n = 1; n <= s->max_iter; ++n) {
+        dr = 2.0 * sqrt(or_modulus(z, s->modulus_mode)) * dr;
+        or_dq_square(z, s->square_mode, sq);
+        or_dq_add(sq, s->c, z);
+        double m = or_modulus(z, s->modulus_mode);
+        if (m > r2) {
+            double a = sqrt(m);
+            if (iters) *iters += n;
+            *dist = 0.5 * a / dr * log(a);
+            return n;
+        }
+    }
+    if (iters) *iters += s->max_iter;
+    *dist = 0.0;
+    return 0;
+}
+
+/* Sphere tracing along the ray (Method, "Ray-Marching"): from the entry into
+ * the box (and the bounding sphere, when its radius is positive), sample,
+ * stop at an inside sample or one whose estimate is below de_epsilon (a hit
+ * at that sample), else advance by de_step_scale times the estimate; a ray
+ * that leaves the volume or runs out of steps misses.  Sets t->hit, t->depth,
+ * t->n_star (escape count at the hit sample, max_iter when inside) and
+ * t->esc_max (the largest escape count over the samples). */
+static void de_trace(const or_scene *s, or_trace *t)
+{
+    double t0 = t->t_in, t1 = t->t_out;
+    if (s->de_bound_radius > 0.0) {
+        double b = v3_dot(t->o, t->d);
+        double c = v3_dot(t->o, t->o) - s->de_bound_radius * s->de_bound_radius;
+        double disc = b * b - c;
+        if (!(disc > 0.0)) return;
+        double q = sqrt(disc);
+        if (-b - q > t0) t0 = -b - q;
+        if (-b + q < t1) t1 = -b + q;
+        if (!(t0 < t1)) return;
+    }
+    double tt = t0, p[3], dist;
+    for (int step = 0; step < s->de_max_steps && tt <= t1; ++step) {
+        ray_point(t->o, t->d, tt, p);
+        int n = or_de_distance(s, p, &dist, &t->class_iters);
+        t->de_steps += 1;
+        if (n == 0 || dist < s->de_epsilon) {
+            t->hit = 1;
+            t->depth = tt;
+            t->n_star = n == 0 ? s->max_iter : n;
+            if (n != 0 && n > t->esc_max) t->esc_max = n;
+            return;
+        }
+        if (n > t->esc_max) t->esc_max = n;
+        tt += s->de_step_scale * dist;
+    }
+}
+
 static void render_pixel(const or_scene *s, int i, int j, pixel_out *po, or_trace *tr)
 {
     or_trace t;
@@ -413,6 +488,18 @@ static void render_pixel(const or_scene *s, int i, int j, pixel_out *po, or_trac
     if (!t.box_hit) {
         if (tr) *tr = t;
         return;
+    }
+
+    int n_star;
+    if (s->traversal == 1) {
+        de_trace(s, &t);
+        if (!t.hit) {
+            po->iter = t.esc_max;
+            if (tr) *tr = t;
+            return;
+        }
+        n_star = t.n_star;
+        goto shade;
     }
 
     /* March: N+1 samples in order, stop at the first inside one. */
@@ -441,7 +528,6 @@ static void render_pixel(const or_scene *s, int i, int j, pixel_out *po, or_trac
     t.hit = 1;
 
     /* Bisection of the first outside -> inside bracket. */
-    int n_star;
     if (t.k_first == 0) {
         t.lo = t.hi = t.depth = t.t_in;
         n_star = s->max_iter;
@@ -466,6 +552,7 @@ static void render_pixel(const or_scene *s, int i, int j, pixel_out *po, or_trac
         n_star = n_lo;
     }
     t.n_star = n_star;
+shade:
     po->iter = n_star;
     po->depth = t.depth;
 

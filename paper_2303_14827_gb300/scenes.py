@@ -17,6 +17,8 @@ import copy
 
 import numpy as np
 
+TRAVERSAL_MARCH = 0  # fixed-step march + bisection
+TRAVERSAL_DE = 1     # distance-estimate sphere tracing (Eq. distfract2)
 PRECISION_FP32 = 0
 PRECISION_FP32_RECHECK = 1
 PRECISION_FP64 = 2
@@ -85,6 +87,11 @@ def default_scene(**overrides) -> dict:
         "modulus_mode": MODULUS_EUCLID8,
         "k_specular": 0.0,
         "shininess": 32.0,
+        "traversal": TRAVERSAL_MARCH,
+        "de_max_steps": 512,
+        "de_epsilon": 1e-3,
+        "de_step_scale": 1.0,
+        "de_bound_radius": 0.0,
     }
     for k, v in overrides.items():
         if k not in s:
