@@ -62,6 +62,21 @@ enum {
     DQJ_SQUARE_PAPER_COMPONENTWISE = 1 /* zeta^2 = q_r^2 + q_d^2 eps, as printed     */
 };
 
+/* dqj_params.traversal (Method, "Ray-Marching").  MARCH: march_steps + 1
+ * equally spaced samples over the box, the first inside one refined by
+ * bisect_steps halvings.  DE: the paper's own traversal, sphere tracing by the
+ * distance estimate of Eq. distfract2, d = 0.5 |zeta_n| / |zeta'_n| ln |zeta_n|
+ * at the escape step n, with |zeta'_{n+1}| = 2 |zeta_n| |zeta'_n| (Eq. distfract)
+ * and |zeta| = sqrt(modulus): from the entry into the box (and the bounding
+ * sphere of radius de_bound_radius, when positive) a ray samples, hits at an
+ * inside sample or one whose estimate is below de_epsilon, otherwise advances
+ * by de_step_scale times the estimate, and misses when it leaves the volume
+ * or after de_max_steps samples.  A hit's depth is its sample's t and n* its
+ * escape count (max_iter when inside); a miss reports the largest escape
+ * count over its samples.  DE supports DQJ_FP32 and DQJ_FP64. */
+#define DQJ_TRAVERSAL_MARCH 0
+#define DQJ_TRAVERSAL_DE 1
+
 /* dqj_params.modulus_mode (Introduction; appendix, magnitude) */
 enum {
     DQJ_MODULUS_EUCLID8 = 0, /* |q_r|^2 + |q_d|^2                                   */
@@ -115,6 +130,11 @@ typedef struct {
     int32_t modulus_mode;       /* DQJ_MODULUS_*                                      */
     double k_specular;          /* Eq. phong specular coefficient k_s >= 0 (0: off)   */
     double shininess;           /* Eq. phong specular exponent s, 0..10000            */
+    int32_t traversal;          /* DQJ_TRAVERSAL_MARCH | DQJ_TRAVERSAL_DE             */
+    int32_t de_max_steps;       /* DE: samples per ray at most, 1..1000000            */
+    double de_epsilon;          /* DE: a sample whose estimate is below this is a hit */
+    double de_step_scale;       /* DE: step = scale * estimate, (0, 1]                */
+    double de_bound_radius;     /* DE: bounding sphere about the origin, 0 = box only */
 } dqj_params;
 
 /*

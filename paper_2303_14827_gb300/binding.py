@@ -72,6 +72,11 @@ class dqj_params(ctypes.Structure):
         ("modulus_mode", ctypes.c_int32),
         ("k_specular", ctypes.c_double),
         ("shininess", ctypes.c_double),
+        ("traversal", ctypes.c_int32),
+        ("de_max_steps", ctypes.c_int32),
+        ("de_epsilon", ctypes.c_double),
+        ("de_step_scale", ctypes.c_double),
+        ("de_bound_radius", ctypes.c_double),
     ]
 
 
@@ -165,6 +170,11 @@ def make_params(scene: dict) -> dqj_params:
         setattr(p, k, float(scene[k]))
     p.k_specular = float(scene.get("k_specular", 0.0))
     p.shininess = float(scene.get("shininess", 32.0))
+    p.traversal = int(scene.get("traversal", 0))
+    p.de_max_steps = int(scene.get("de_max_steps", 512))
+    p.de_epsilon = float(scene.get("de_epsilon", 1e-3))
+    p.de_step_scale = float(scene.get("de_step_scale", 1.0))
+    p.de_bound_radius = float(scene.get("de_bound_radius", 0.0))
     for k in ("width", "height", "max_iter", "march_steps", "bisect_steps", "precision", "square_mode",
               "modulus_mode"):
         setattr(p, k, int(scene[k]))

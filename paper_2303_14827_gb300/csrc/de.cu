@@ -1,0 +1,211 @@
+// de.cu -- the paper's own traversal: sphere tracing by the distance estimate
+// (Method, "Ray-Marching", Eq. distfract2 with the derivative recurrence of
+// Eq. distfract), and the normal + shading pass over its hits.
+//
+// One ray per lane over 8x4 screen tiles claimed by warps of a persistent grid.
+// Every lane advances its own ray (its own t); a round samples every active
+// ray once, iterating in lockstep until no lane still has a bounded sample,
+// and ends when no lane is active.  The derivative is carried squared,
+// |zeta'_{n+1}|^2 = 4 |zeta_n|^2 |zeta'_n|^2, so a step needs no square root;
+// the estimate 0.5 |zeta| / |zeta'| ln |zeta| = 0.25 sqrt(m / dr2) ln m is
+// formed once per sample from the modulus m and dr2 at the escape step.  (In
+// FP32 dr2 overflows only past ~21 steps, where the estimate is ~1e-15: an
+// overflow gives 0, which is below any epsilon, the same decision.)
+// Hits go to the hit list as (pixel, depth bits, n*); misses write their
+// planes directly.
+#include "render_common.cuh"
+#include "runtime.h"
+
+namespace dqj {
+
+namespace {
+
+constexpr int kDeTileW = 8, kDeTileH = 4;
+
+// Lockstep classification with the squared derivative: returns the escape
+// count (0 = inside) and, for an escaped sample, the distance estimate.
+template <typename T, int SQ, int MOD>
+__device__ __forceinline__ int classify_de(T (&z)[8], const FrameT<T> &F, int max_iter, bool part, T &dist)
+{
+    bool alive = part;
+    int cnt = 0;
+    T sp = dq_sp<T>(z);
+    T m = modulus<T, MOD>(z);
+    T dr2 = T(1), m_esc = T(0), dr2_esc = T(1);
+    for (int n = 0; n < max_iter; ++n) {
+        dr2 = T(4) * m * dr2;
+        m = dq_iter<T, SQ, MOD>(z, z, sp, F.c);
+        const bool esc = alive && !(m <= F.R2);
+        if (esc) {
+            m_esc = m;
+            dr2_esc = dr2;
+        }
+        alive = alive && (m <= F.R2);
+        cnt += alive ? 1 : 0;
+        if (!__any_sync(kFull, alive)) break;
+    }
+    if (!part || alive) {
+        dist = T(0);
+        return 0;
+    }
+    dist = T(0.25) * sqrt(m_esc / dr2_esc) * log(m_esc);
+    return cnt + 1;
+}
+
+template <typename T, int SQ, int MOD>
+__global__ void __launch_bounds__(kBlock) de_kernel(const __grid_constant__ FrameDesc fd, const Scratch sc)
+{
+    const FrameT<T> &F = frame<T>(fd);
+    const int lane = threadIdx.x & 31;
+    const int tiles_x = (fd.W + kDeTileW - 1) / kDeTileW;
+    const unsigned ntiles = (unsigned)tiles_x * (unsigned)((fd.H + kDeTileH - 1) / kDeTileH);
+    LaneStats st;
+    for (;;) {
+        unsigned tile = 0;
+        if (lane == 0) tile = atomicAdd(&sc.ctr->tile_next, 1u);
+        tile = __shfl_sync(kFull, tile, 0);
+        if (tile >= ntiles) break;
+        const int x = (int)(tile % (unsigned)tiles_x) * kDeTileW + lane % kDeTileW;
+        const int y = (int)(tile / (unsigned)tiles_x) * kDeTileH + lane / kDeTileW;
+        const bool valid = x < fd.W && y < fd.H;
+        T d[3] = {T(0), T(0), T(1)};
+        T t0 = T(0), t1 = T(0);
+        bool act = valid && camera_clip<T>(F, fd.W, fd.H, x, y, d, t0, t1);
+        if (act && F.de_rb > T(0)) {  // bounding sphere about the origin
+            const T b = F.eye[0] * d[0] + F.eye[1] * d[1] + F.eye[2] * d[2];
+            const T c = F.eye[0] * F.eye[0] + F.eye[1] * F.eye[1] + F.eye[2] * F.eye[2] - F.de_rb * F.de_rb;
+            const T disc = b * b - c;
+            if (disc > T(0)) {
+                const T q = sqrt(disc);
+                t0 = max(t0, -b - q);
+                t1 = min(t1, -b + q);
+                act = t0 < t1;
+            } else {
+                act = false;
+            }
+        }
+        T D[8];
+        slice_dir<T>(F, d, D);
+        T t = t0, depth = T(0);
+        int steps = 0, esc_max = 0, n_star = 0;
+        bool hit = false;
+        while (__any_sync(kFull, act)) {
+            T z[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) z[i] = dfma(t, D[i], F.A[i]);
+            T dist;
+            const int n = classify_de<T, SQ, MOD>(z, F, fd.max_iter, act, dist);
+            if (act) {
+                ++steps;
+                st.iters += n ? (unsigned)n : (unsigned)fd.max_iter;
+                if (n > esc_max) esc_max = n;
+                if (n == 0 || dist < F.de_eps) {
+                    hit = true;
+                    depth = t;
+                    n_star = n ? n : fd.max_iter;
+                    act = false;
+                } else {
+                    t = t + F.de_scale * dist;
+                    act = steps < fd.de_max_steps && t <= t1;
+                }
+            }
+        }
+        st.samples += (unsigned)steps;
+        st.hits += hit ? 1 : 0;
+        if (valid && !hit) write_miss<T>(fd, x, y, esc_max);
+        int4 e = make_int4(y * fd.W + x, 0, 0, n_star);
+        if constexpr (sizeof(T) == 8) {
+            const long long b = __double_as_longlong((double)depth);
+            e.y = (int)(unsigned)(b & 0xffffffffll);
+            e.z = (int)(b >> 32);
+        } else {
+            e.y = __float_as_int((float)depth);
+        }
+        warp_push(hit, e, sc.hits, sc.hit_cap, &sc.ctr->hit_count);
+    }
+    flush_lane_stats<false>(sc, st, true);
+}
+
+template <typename T, int SQ, int MOD>
+__global__ void __launch_bounds__(kBlock) de_shade_kernel(const __grid_constant__ FrameDesc fd, const Scratch sc)
+{
+    const FrameT<T> &F = frame<T>(fd);
+    const int lane = threadIdx.x & 31;
+    const unsigned nhits = min(*(volatile unsigned *)&sc.ctr->hit_count, sc.hit_cap);
+    LaneStats st;
+    for (;;) {
+        unsigned base = 0;
+        if (lane == 0) base = atomicAdd(&sc.ctr->hit_next, 32u);
+        base = __shfl_sync(kFull, base, 0);
+        if (base >= nhits) break;
+        const unsigned idx = base + lane;
+        const bool part = idx < nhits;
+        int4 e = make_int4(0, 0, 0, 0);
+        if (part) e = __ldcg(sc.hits + idx);
+        const int x = e.x % fd.W, y = e.x / fd.W;
+        T depth;
+        if constexpr (sizeof(T) == 8)
+            depth = __longlong_as_double(((long long)e.z << 32) | (long long)(unsigned)e.y);
+        else
+            depth = __int_as_float(e.y);
+        T d[3] = {T(0), T(0), T(1)};
+        T t_in, t_out;
+        if (part) camera_clip<T>(F, fd.W, fd.H, x, y, d, t_in, t_out);
+        T D[8];
+        slice_dir<T>(F, d, D);
+        normal_shade<T, SQ, MOD>(fd, F, x, y, d, D, part ? depth : T(0), e.w, part, st);
+    }
+    flush_stat(&sc.ctr->stats[1], st.niters);
+}
+
+template <typename K>
+int de_grid(K kernel, int num_sms)
+{
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, 0) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    return per_sm * num_sms;
+}
+
+template <typename T, int SQ, int MOD>
+cudaError_t launch_de_t(const FrameDesc &fd, const Scratch &sc, cudaStream_t st, int num_sms, cudaEvent_t *ev)
+{
+    static int g_de = 0, g_sh = 0;
+    if (!g_de) g_de = de_grid(de_kernel<T, SQ, MOD>, num_sms);
+    if (!g_sh) g_sh = de_grid(de_shade_kernel<T, SQ, MOD>, num_sms);
+    const unsigned ntiles = (unsigned)((fd.W + kDeTileW - 1) / kDeTileW) * (unsigned)((fd.H + kDeTileH - 1) / kDeTileH);
+    const int gd = (int)min((unsigned)g_de, (ntiles + 3u) / 4u);
+    const unsigned maxw = ((unsigned)fd.W * (unsigned)fd.H + 31u) / 32u;
+    const int gs = (int)min((unsigned)g_sh, (maxw + 3u) / 4u);
+    if (ev) cudaEventRecord(ev[0], st);
+    de_kernel<T, SQ, MOD><<<gd > 0 ? gd : 1, kBlock, 0, st>>>(fd, sc);
+    if (ev) cudaEventRecord(ev[1], st);
+    de_shade_kernel<T, SQ, MOD><<<gs > 0 ? gs : 1, kBlock, 0, st>>>(fd, sc);
+    if (ev) {
+        cudaEventRecord(ev[2], st);
+        cudaEventRecord(ev[3], st);
+        cudaEventRecord(ev[4], st);
+    }
+    return cudaGetLastError();
+}
+
+template <int SQ, int MOD>
+cudaError_t launch_de_m(const FrameDesc &fd, const Scratch &sc, cudaStream_t st, int num_sms, cudaEvent_t *ev)
+{
+    return fd.precision == DQJ_FP64 ? launch_de_t<double, SQ, MOD>(fd, sc, st, num_sms, ev)
+                                    : launch_de_t<float, SQ, MOD>(fd, sc, st, num_sms, ev);
+}
+
+}  // namespace
+
+cudaError_t launch_de(const FrameDesc &fd, const Scratch &sc, cudaStream_t st, int num_sms, cudaEvent_t *ev)
+{
+    switch (fd.square_mode * 2 + fd.modulus_mode) {
+    case 0: return launch_de_m<0, 0>(fd, sc, st, num_sms, ev);
+    case 1: return launch_de_m<0, 1>(fd, sc, st, num_sms, ev);
+    case 2: return launch_de_m<1, 0>(fd, sc, st, num_sms, ev);
+    default: return launch_de_m<1, 1>(fd, sc, st, num_sms, ev);
+    }
+}
+
+}  // namespace dqj

@@ -30,6 +30,7 @@ struct FrameT {
     T light[3];    // unit vector to the light
     T ka, kd, albedo[3];
     T ks, shin;  // Eq. phong specular coefficient and exponent (ks = 0: off)
+    T de_eps, de_scale, de_rb;  // distance-estimate traversal: hit threshold, step scale, bounding radius
 };
 
 // Encoding of a queued FP64 recheck: which sample of which pixel.
@@ -53,6 +54,8 @@ struct alignas(16) FrameDesc {
     int32_t square_mode, modulus_mode, precision;
     int32_t march_variant;   // FP32 march: 0 one ray per lane, 1 two rays per lane (paired FP32)
     int32_t tile_w, tile_h, tiles_x, tiles_y;
+    int32_t traversal;       // DQJ_TRAVERSAL_MARCH or DQJ_TRAVERSAL_DE
+    int32_t de_max_steps;
     int64_t pitch;
     int32_t *iter;
     float *depth;
@@ -94,6 +97,9 @@ struct alignas(16) Scratch {
 // before the march and after the march, bisect, recheck and fixup passes.
 cudaError_t launch_frame(const FrameDesc &fd, const Scratch &sc, cudaStream_t st, int num_sms,
                          cudaEvent_t *ev = nullptr);
+// The distance-estimate traversal (de.cu): sphere tracing, then normal and
+// shading of its hits; same events (the last three after the shading pass).
+cudaError_t launch_de(const FrameDesc &fd, const Scratch &sc, cudaStream_t st, int num_sms, cudaEvent_t *ev);
 cudaError_t fma_peak_launch(int variant, int num_sms, float *sink, cudaStream_t st, double *flops);
 
 }  // namespace dqj

@@ -22,6 +22,7 @@
 #include <cstdio>
 
 #include "render_common.cuh"
+#include "../../include/dqj.h"
 
 namespace dqj {
 
@@ -332,6 +333,7 @@ cudaError_t launch_mode(const FrameDesc &fd, const Scratch &sc, cudaStream_t st,
 
 cudaError_t launch_frame(const FrameDesc &fd, const Scratch &sc, cudaStream_t st, int num_sms, cudaEvent_t *ev)
 {
+    if (fd.traversal == DQJ_TRAVERSAL_DE) return launch_de(fd, sc, st, num_sms, ev);
     const int m = fd.square_mode * 2 + fd.modulus_mode;
     switch (m) {
     case 0: return launch_mode<0, 0>(fd, sc, st, num_sms, ev);

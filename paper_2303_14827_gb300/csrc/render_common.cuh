@@ -284,6 +284,42 @@ __device__ __forceinline__ void march2_tile(const FrameDesc &fd, const PairConst
     warp_push(hitb, make_int4(yb * fd.W + xb, kfb, prevb + 1, 0), sc.hits, sc.hit_cap, &sc.ctr->hit_count);
 }
 
+// Normal (central differences of F(p) = modulus(zeta_{n*}(p)) at p +- h e_a,
+// iterated n* times from zeta0 = A + depth D +- h E_a, the slice image of
+// eye + depth d +- h e_a), shading and the pixel's outputs for a hit at depth;
+// lanes with part == false only join the warp-wide loop bound.
+template <typename T, int SQ, int MOD>
+__device__ __forceinline__ void normal_shade(const FrameDesc &fd, const FrameT<T> &F, int x, int y, const T (&d)[3],
+                                             const T (&D)[8], T depth, int n_star, bool part, LaneStats &st)
+{
+    int nmax = part ? n_star : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nmax = max(nmax, __shfl_xor_sync(kFull, nmax, o));
+    T g[3];
+    bool guard = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        T fv[2];
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            const T hs = s == 0 ? F.h : -F.h;
+            T z[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) z[i] = dfma(hs, F.E[a][i], dfma(depth, D[i], F.A[i]));
+            T sp = dq_sp<T>(z);
+            for (int n = 0; n < nmax; ++n)
+                if (n < n_star) dq_iter<T, SQ, MOD>(z, z, sp, F.c);
+            fv[s] = modulus<T, MOD>(z);
+            guard = guard || !(fv[s] <= normal_fmax(T(0)));
+        }
+        g[a] = fv[0] - fv[1];
+    }
+    if (part) {
+        st.niters += 6ull * (unsigned)n_star;
+        shade_write<T>(fd, F, x, y, n_star, depth, g, guard, d);
+    }
+}
+
 // Bisection, normal and shading of hit-list entries [base, base + 32) clipped to
 // nhits, one per lane (see bisect_kernel); all 32 lanes call.
 template <typename T, int SQ, int MOD, bool RECHECK>
@@ -339,35 +375,7 @@ __device__ __forceinline__ void bisect_chunk(const FrameDesc &fd, const Scratch 
         }
     }
     const T depth = bis ? lo + T(0.5) * (hi - lo) : t_in;
-    const int n_star = n_lo;
-    // Normal: F(p) = modulus(zeta_{n*}(p)) at p +- h e_a, iterated n* times.
-    // zeta0 = A + depth D +- h E_a (the slice image of eye + depth d +- h e_a).
-    int nmax = part ? n_star : 0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) nmax = max(nmax, __shfl_xor_sync(kFull, nmax, o));
-    T g[3];
-    bool guard = false;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        T fv[2];
-#pragma unroll
-        for (int s = 0; s < 2; ++s) {
-            const T hs = s == 0 ? F.h : -F.h;
-            T z[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) z[i] = dfma(hs, F.E[a][i], dfma(depth, D[i], F.A[i]));
-            T sp = dq_sp<T>(z);
-            for (int n = 0; n < nmax; ++n)
-                if (n < n_star) dq_iter<T, SQ, MOD>(z, z, sp, F.c);
-            fv[s] = modulus<T, MOD>(z);
-            guard = guard || !(fv[s] <= normal_fmax(T(0)));
-        }
-        g[a] = fv[0] - fv[1];
-    }
-    if (part) {
-        st.niters += 6ull * (unsigned)n_star;
-        shade_write<T>(fd, F, x, y, n_star, depth, g, guard, d);
-    }
+    normal_shade<T, SQ, MOD>(fd, F, x, y, d, D, depth, n_lo, part, st);
     st.iters += iters;
     st.samples += samples;
 }

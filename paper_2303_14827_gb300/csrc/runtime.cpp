@@ -82,6 +82,19 @@ dqj_status validate(const dqj_params *p)
     if (!(p->k_specular >= 0.0 && p->k_specular <= 1e6))
         return fail(DQJ_ERR_INVALID, "k_specular must be finite and >= 0");
     if (!(p->shininess >= 0.0 && p->shininess <= 1e4)) return fail(DQJ_ERR_INVALID, "shininess must be in [0, 10000]");
+    if (p->traversal != DQJ_TRAVERSAL_MARCH && p->traversal != DQJ_TRAVERSAL_DE)
+        return fail(DQJ_ERR_INVALID, "traversal must be DQJ_TRAVERSAL_MARCH or DQJ_TRAVERSAL_DE");
+    if (p->traversal == DQJ_TRAVERSAL_DE) {
+        if (p->precision == DQJ_FP32_RECHECK)
+            return fail(DQJ_ERR_INVALID, "DQJ_TRAVERSAL_DE supports DQJ_FP32 and DQJ_FP64 only");
+        if (p->de_max_steps < 1 || p->de_max_steps > 1000000)
+            return fail(DQJ_ERR_INVALID, "de_max_steps must be in 1..1000000");
+        if (!(p->de_epsilon > 0.0 && p->de_epsilon < 1e30)) return fail(DQJ_ERR_INVALID, "de_epsilon must be > 0");
+        if (!(p->de_step_scale > 0.0 && p->de_step_scale <= 1.0))
+            return fail(DQJ_ERR_INVALID, "de_step_scale must be in (0, 1]");
+        if (!(p->de_bound_radius >= 0.0 && p->de_bound_radius < 1e30))
+            return fail(DQJ_ERR_INVALID, "de_bound_radius must be >= 0");
+    }
     for (int a = 0; a < 3; ++a)
         if (!(p->albedo[a] >= 0.0 && p->albedo[a] <= 1.0)) return fail(DQJ_ERR_INVALID, "albedo must be in [0, 1]");
     return DQJ_OK;
@@ -150,6 +163,9 @@ void derive_frame(const dqj_params &p, FrameDesc &fd, int tile_w, int tile_h)
     F.kd = p.k_diffuse;
     F.ks = p.k_specular;
     F.shin = p.shininess;
+    F.de_eps = p.de_epsilon;
+    F.de_scale = p.de_step_scale;
+    F.de_rb = p.de_bound_radius;
     cast_frame<float>(F, fd.f);
     for (int i = 0; i < 8; ++i) {
         fd.p2.c[i] = make_float2(fd.f.c[i], fd.f.c[i]);
@@ -165,6 +181,8 @@ void derive_frame(const dqj_params &p, FrameDesc &fd, int tile_w, int tile_h)
     fd.square_mode = p.square_mode;
     fd.modulus_mode = p.modulus_mode;
     fd.precision = p.precision;
+    fd.traversal = p.traversal;
+    fd.de_max_steps = p.de_max_steps;
     fd.tile_w = tile_w;
     fd.tile_h = tile_h;
     fd.tiles_x = (p.width + tile_w - 1) / tile_w;
@@ -361,6 +379,11 @@ dqj_status dqj_default_params(dqj_params *p)
     p->modulus_mode = DQJ_MODULUS_EUCLID8;
     p->k_specular = 0.0;
     p->shininess = 32.0;
+    p->traversal = DQJ_TRAVERSAL_MARCH;
+    p->de_max_steps = 512;
+    p->de_epsilon = 1e-3;
+    p->de_step_scale = 1.0;
+    p->de_bound_radius = 0.0;
     return DQJ_OK;
 }
 

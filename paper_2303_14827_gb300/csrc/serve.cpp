@@ -57,7 +57,8 @@ struct Request {
 
 bool packable(const dqj_params &p)
 {
-    return p.precision == DQJ_FP32 && p.square_mode == DQJ_SQUARE_ALGEBRAIC && p.modulus_mode == DQJ_MODULUS_EUCLID8;
+    return p.precision == DQJ_FP32 && p.square_mode == DQJ_SQUARE_ALGEBRAIC && p.modulus_mode == DQJ_MODULUS_EUCLID8 &&
+           p.traversal == DQJ_TRAVERSAL_MARCH;
 }
 
 uint64_t scratch_bytes(const dqj_params &p, bool packed)

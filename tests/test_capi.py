@@ -94,3 +94,20 @@ def test_voxelize_validation_on_a_mock_context(monkeypatch):
         binding.dqj_destroy(ctx)
     text = open(binding.HEADER).read()
     assert re.search(r"#define DQJ_VOXEL_MAX_GRID (\d+)", text).group(1) == str(binding.DQJ_VOXEL_MAX_GRID)
+
+
+@pytest.mark.parametrize("field,value", [("traversal", 2), ("de_max_steps", 0), ("de_epsilon", 0.0),
+                                         ("de_step_scale", 1.5), ("de_step_scale", 0.0), ("de_bound_radius", -1.0)])
+def test_de_validation_rejects(lib, field, value):
+    s = scenes.default_scene(traversal=scenes.TRAVERSAL_DE)
+    s[field] = value
+    p = binding.make_params(s)
+    assert lib.dqj_validate_params(binding.ctypes.byref(p)) == binding.DQJ_ERR_INVALID
+    assert field.split("_")[0] in binding.last_error()
+
+
+def test_de_rejects_recheck_precision(lib):
+    p = binding.make_params(scenes.default_scene(traversal=scenes.TRAVERSAL_DE,
+                                                 precision=scenes.PRECISION_FP32_RECHECK))
+    assert lib.dqj_validate_params(binding.ctypes.byref(p)) == binding.DQJ_ERR_INVALID
+    assert "DQJ_TRAVERSAL_DE" in binding.last_error()
