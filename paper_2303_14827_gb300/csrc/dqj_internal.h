@@ -83,7 +83,7 @@ static_assert(sizeof(Counters) == 128, "Counters layout");
 // Views into one scratch allocation owned by a context.
 struct alignas(16) Scratch {
     Counters *ctr;
-    int4 *hits;           // {pixel, k_first, n_prev, 0}
+    int4 *hits;           // march: {pixel, k_first, 0, 0}; sphere tracing: {pixel, depth bits, n*}
     uint32_t hit_cap;
     int4 *queue;          // {pixel, k | b << 16, path, n32}
     uint32_t queue_cap;

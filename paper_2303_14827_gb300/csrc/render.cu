@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(kBlock) march_kernel(const __grid_constant__ F
         T D[8];
         slice_dir<T>(F, d, D);
         const T delta = (t_out - t_in) / T(fd.N);
-        int esc_max = 0, n_prev = 0, k_first = -1;
+        int esc_max = 0, k_first = -1;
         unsigned iters = 0, samples = 0;
         for (int k = 0; k <= fd.N; ++k) {
             if (!__any_sync(kFull, active)) break;
@@ -81,7 +81,6 @@ __global__ void __launch_bounds__(kBlock) march_kernel(const __grid_constant__ F
                     active = false;
                 } else {
                     esc_max = n > esc_max ? n : esc_max;
-                    n_prev = n;
                 }
             }
         }
@@ -90,7 +89,7 @@ __global__ void __launch_bounds__(kBlock) march_kernel(const __grid_constant__ F
         const bool hit = valid && k_first >= 0;
         if (valid && !hit) write_miss<T>(fd, x, y, esc_max);
         s_hits += hit ? 1 : 0;
-        warp_push(hit, make_int4(y * fd.W + x, k_first, n_prev, 0), sc.hits, sc.hit_cap, &sc.ctr->hit_count);
+        warp_push(hit, make_int4(y * fd.W + x, k_first, 0, 0), sc.hits, sc.hit_cap, &sc.ctr->hit_count);
     }
     flush_stat(&sc.ctr->stats[0], s_iters);
     flush_stat(&sc.ctr->stats[8], s_iters);
@@ -104,9 +103,10 @@ __global__ void __launch_bounds__(kBlock) march_kernel(const __grid_constant__ F
 // 64-ray tile, advanced together in the two halves of float2 registers by the
 // paired FP32 instructions.  Same per-ray arithmetic as march_kernel<float>.
 // Per ray it keeps only running sums: sum_* (steps stayed bounded, summed over
-// samples), max_* (largest escape count - 1), prev_* (escape count - 1 of the
-// latest outside sample) and the first inside sample kf_*; the iteration and
-// sample counts follow from them once the ray is done.
+// samples), max_* (largest escape count - 1) and the first inside sample kf_*;
+// the iteration and sample counts follow from them once the ray is done.  The
+// escape count of the sample before a hit is classified again by the
+// bisection pass, which needs it only for hits.
 // ---------------------------------------------------------------------------
 template <int SQ, int MOD, bool RECHECK, bool AXIS>
 __global__ void __launch_bounds__(kBlock, 5) march2_kernel(const __grid_constant__ FrameDesc fd, const Scratch sc)

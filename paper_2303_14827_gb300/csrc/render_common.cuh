@@ -233,7 +233,7 @@ __device__ __forceinline__ void march2_tile(const FrameDesc &fd, const PairConst
     const float2 tin = make_float2(tia, tib);
     const float2 dl = make_float2((toa - tia) / (float)N, (tob - tib) / (float)N);
     bool acta = boxa, actb = boxb;
-    int suma = 0, sumb = 0, maxa = 0, maxb = 0, preva = 0, prevb = 0, kfa = -1, kfb = -1;
+    int suma = 0, sumb = 0, maxa = 0, maxb = 0, kfa = -1, kfb = -1;
     float2 kf = make_float2(0.f, 0.f);
     for (int k = 0; k <= N; ++k) {
         if (!__any_sync(kFull, acta || actb)) break;
@@ -264,8 +264,6 @@ __device__ __forceinline__ void march2_tile(const FrameDesc &fd, const PairConst
         sumb += cb;
         maxa = max(maxa, ca);
         maxb = max(maxb, cb);
-        if (acta && !ina) preva = ca;
-        if (actb && !inb) prevb = cb;
         if (ina) kfa = k;
         if (inb) kfb = k;
         acta = acta && !ina;
@@ -280,8 +278,8 @@ __device__ __forceinline__ void march2_tile(const FrameDesc &fd, const PairConst
     st.hits += (hita ? 1 : 0) + (hitb ? 1 : 0);
     if (va && !hita) write_miss<float>(fd, xa, ya, boxa ? maxa + 1 : 0);
     if (vb && !hitb) write_miss<float>(fd, xb, yb, boxb ? maxb + 1 : 0);
-    warp_push(hita, make_int4(ya * fd.W + xa, kfa, preva + 1, 0), sc.hits, sc.hit_cap, &sc.ctr->hit_count);
-    warp_push(hitb, make_int4(yb * fd.W + xb, kfb, prevb + 1, 0), sc.hits, sc.hit_cap, &sc.ctr->hit_count);
+    warp_push(hita, make_int4(ya * fd.W + xa, kfa, 0, 0), sc.hits, sc.hit_cap, &sc.ctr->hit_count);
+    warp_push(hitb, make_int4(yb * fd.W + xb, kfb, 0, 0), sc.hits, sc.hit_cap, &sc.ctr->hit_count);
 }
 
 // Normal (central differences of F(p) = modulus(zeta_{n*}(p)) at p +- h e_a,
@@ -343,7 +341,18 @@ __device__ __forceinline__ void bisect_chunk(const FrameDesc &fd, const Scratch 
     bool bis = part && k_first > 0;
     T lo = bis ? dfma(T(k_first - 1), delta, t_in) : t_in;
     T hi = bis ? dfma(T(k_first), delta, t_in) : t_in;
-    int n_lo = bis ? e.z : fd.max_iter;
+    // n* starts as the escape count of the last outside march sample, k_first - 1:
+    // the march keeps no per-sample counts, so it is classified again here, with
+    // the march's own position and arithmetic (not counted as new iterations)
+    int n_lo = fd.max_iter;
+    {
+        T z[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) z[i] = dfma(lo, D[i], F.A[i]);
+        bool mg;
+        const int n = classify_lockstep<T, SQ, MOD, false>(z, F, fd.max_iter, bis, mg);
+        if (bis) n_lo = n;
+    }
     unsigned path = 0;
     unsigned iters = 0, samples = 0;
     for (int b = 0; b < fd.B; ++b) {
