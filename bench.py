@@ -325,13 +325,12 @@ def run_gpu(args, world, rank, local):
                 "rgba": torch.empty((H, W, 4), dtype=torch.uint8).pin_memory(),
                 "stats": torch.zeros(binding.DQJ_NSTATS, dtype=torch.int64).pin_memory(),
                 "pitch_px": W})
-        for s, o in zip(frames, host):  # warm-up of the host path
-            binding.dqj_render_host(ctx, s, binding.outputs_of(o))
+        host_outs = [binding.outputs_of(o) for o in host]
+        binding.dqj_render_host_batch(ctx, frames, host_outs)  # warm-up of the host path
         barrier(world)
         t0 = time.perf_counter()
-        for _ in range(args.steps):
-            for s, o in zip(frames, host):
-                binding.dqj_render_host(ctx, s, binding.outputs_of(o))
+        for _ in range(args.steps):  # one step: the five frames, copies back overlapped with the next render
+            binding.dqj_render_host_batch(ctx, frames, host_outs)
         dt = max_over_ranks(time.perf_counter() - t0, world)
         e2e_iters = sum(int(o["stats"][0]) + int(o["stats"][1]) for o in host)
         line["e2e"] = {"value": e2e_iters * args.steps * world / dt, "unit": UNIT,

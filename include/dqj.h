@@ -201,6 +201,15 @@ dqj_status dqj_render(dqj_ctx *ctx, const dqj_params *p, const dqj_outputs *out,
  * device planes, copies the requested planes to the host and waits.  Blocking. */
 dqj_status dqj_render_host(dqj_ctx *ctx, const dqj_params *p, const dqj_outputs *host_out);
 
+/* Render n frames into HOST buffers, p[i] into host_out[i], and wait.  The
+ * context keeps two device plane sets, so the copy back of frame i overlaps
+ * the render of frame i + 1 (use page-locked host buffers for the overlap).
+ * Every frame is validated before any work starts (DQJ_ERR_INVALID); results
+ * equal n calls of dqj_render_host.  n = 0 does nothing.  Blocking.  An
+ * interface of this library (throughput for host-resident outputs); the paper
+ * has no counterpart. */
+dqj_status dqj_render_host_batch(dqj_ctx *ctx, const dqj_params *p, const dqj_outputs *host_out, int32_t n);
+
 /* Serving: queue a request and return a ticket at once.  Outputs are
  * caller-owned device memory that must stay valid until dqj_poll reports done
  * and must have no pending work on any stream at submit: the library writes

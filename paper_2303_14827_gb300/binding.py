@@ -122,6 +122,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         L.dqj_create.argtypes = [P(dqj_config), P(ctypes.c_void_p)]
         L.dqj_render.argtypes = [ctypes.c_void_p, P(dqj_params), P(dqj_outputs), ctypes.c_void_p]
         L.dqj_render_host.argtypes = [ctypes.c_void_p, P(dqj_params), P(dqj_outputs)]
+        L.dqj_render_host_batch.argtypes = [ctypes.c_void_p, P(dqj_params), P(dqj_outputs), ctypes.c_int32]
         L.dqj_submit.argtypes = [ctypes.c_void_p, P(dqj_params), P(dqj_outputs), P(ctypes.c_uint64)]
         L.dqj_poll.argtypes = [ctypes.c_void_p, ctypes.c_uint64, P(ctypes.c_int), P(ctypes.c_int)]
         L.dqj_destroy.argtypes = [ctypes.c_void_p]
@@ -241,6 +242,17 @@ def dqj_render(ctx: int, scene: dict, outputs: dqj_outputs, stream: int = 0) -> 
 def dqj_render_host(ctx: int, scene: dict, outputs: dqj_outputs) -> None:
     p = make_params(scene)
     check(load().dqj_render_host(ctypes.c_void_p(ctx), ctypes.byref(p), ctypes.byref(outputs)))
+
+
+def dqj_render_host_batch(ctx: int, scenes: list, outputs: list) -> None:
+    """Render scenes[i] into the HOST buffers outputs[i] (dqj_outputs), copies
+    overlapped with the next frame's render; blocking."""
+    n = len(scenes)
+    if len(outputs) != n:
+        raise ValueError("scenes and outputs differ in length")
+    ps = (dqj_params * max(n, 1))(*[make_params(s) for s in scenes])
+    os_ = (dqj_outputs * max(n, 1))(*outputs)
+    check(load().dqj_render_host_batch(ctypes.c_void_p(ctx), ps, os_, int(n)))
 
 
 DQJ_NOALLOC_MAX_PIXELS = 262144

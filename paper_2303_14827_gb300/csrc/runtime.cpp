@@ -438,53 +438,90 @@ dqj_status dqj_render(dqj_ctx *ctx, const dqj_params *p, const dqj_outputs *out,
     return render_on_stream(ctx, p, out, static_cast<cudaStream_t>(cuda_stream));
 }
 
-dqj_status dqj_render_host(dqj_ctx *ctx, const dqj_params *p, const dqj_outputs *host_out)
+dqj_status dqj_render_host_batch(dqj_ctx *ctx, const dqj_params *p, const dqj_outputs *host_out, int32_t n)
 {
     if (!ctx) return fail(DQJ_ERR_INVALID, "ctx is NULL");
     if (ctx->device == DQJ_DEVICE_MOCK) return fail(DQJ_ERR_INVALID, "a mock context cannot render");
-    dqj_status s = validate(p);
-    if (s != DQJ_OK) return s;
-    s = check_outputs(*p, host_out);
-    if (s != DQJ_OK) return s;
+    if (n < 0 || (n > 0 && (!p || !host_out))) return fail(DQJ_ERR_INVALID, "bad frame count or NULL arrays");
+    size_t need = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        dqj_status s = validate(&p[i]);
+        if (s != DQJ_OK) return s;
+        s = check_outputs(p[i], &host_out[i]);
+        if (s != DQJ_OK) return s;
+        const size_t px = (size_t)p[i].width * (size_t)p[i].height;
+        need = std::max(need, align_up(px * 24, 256) + DQJ_NSTATS * sizeof(int64_t));
+    }
+    if (n == 0) return DQJ_OK;
     std::lock_guard<std::mutex> lk(ctx->mu);
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_fail(e, "render_host: cudaSetDevice");
-    const size_t px = (size_t)p->width * (size_t)p->height;
-    const size_t need = px * 24 + 256 + DQJ_NSTATS * sizeof(int64_t);
-    if (need > ctx->host_planes_bytes) {
-        e = cudaStreamSynchronize(ctx->host_stream);
-        if (e == cudaSuccess && ctx->host_planes) e = cudaFree(ctx->host_planes);
-        ctx->host_planes = nullptr;
-        ctx->host_planes_bytes = 0;
-        if (e == cudaSuccess) e = cudaMalloc(&ctx->host_planes, need);
-        if (e != cudaSuccess) return cuda_fail(e, "render_host: device planes");
-        ctx->host_planes_bytes = need;
+    if (!ctx->host_copy_stream) e = cudaStreamCreateWithFlags(&ctx->host_copy_stream, cudaStreamNonBlocking);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+        if (!ctx->host_rendered[b]) e = cudaEventCreateWithFlags(&ctx->host_rendered[b], cudaEventDisableTiming);
+        if (e == cudaSuccess && !ctx->host_copied[b])
+            e = cudaEventCreateWithFlags(&ctx->host_copied[b], cudaEventDisableTiming);
     }
-    char *b = static_cast<char *>(ctx->host_planes);
-    dqj_outputs dev{};
-    dev.pitch_px = p->width;
-    dev.iter = host_out->iter ? reinterpret_cast<int32_t *>(b) : nullptr;
-    dev.depth = host_out->depth ? reinterpret_cast<float *>(b + px * 4) : nullptr;
-    dev.normal = host_out->normal ? reinterpret_cast<float *>(b + px * 8) : nullptr;
-    dev.rgba = host_out->rgba ? reinterpret_cast<uint8_t *>(b + px * 20) : nullptr;
-    dev.stats = host_out->stats ? reinterpret_cast<int64_t *>(b + align_up(px * 24, 256)) : nullptr;
-    cudaStream_t st = ctx->host_stream;
-    s = enqueue_frame(ctx, *p, dev, st);
-    if (s != DQJ_OK) return s;
-    const size_t w = (size_t)p->width, hp = (size_t)host_out->pitch_px;
-    auto copy2d = [&](void *dst, const void *src, size_t elem) {
-        return cudaMemcpy2DAsync(dst, hp * elem, src, w * elem, w * elem, (size_t)p->height, cudaMemcpyDeviceToHost,
-                                 st);
-    };
-    if (e == cudaSuccess && host_out->iter) e = copy2d(host_out->iter, dev.iter, 4);
-    if (e == cudaSuccess && host_out->depth) e = copy2d(host_out->depth, dev.depth, 4);
-    if (e == cudaSuccess && host_out->normal) e = copy2d(host_out->normal, dev.normal, 12);
-    if (e == cudaSuccess && host_out->rgba) e = copy2d(host_out->rgba, dev.rgba, 4);
-    if (e == cudaSuccess && host_out->stats)
-        e = cudaMemcpyAsync(host_out->stats, dev.stats, DQJ_NSTATS * sizeof(int64_t), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "render_host: streams and events");
+    const int nbuf = n > 1 ? 2 : 1;
+    for (int b = 0; b < nbuf; ++b) {
+        if (need <= ctx->host_planes_bytes[b]) continue;
+        e = cudaStreamSynchronize(ctx->host_copy_stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->host_stream);
+        if (e == cudaSuccess && ctx->host_planes[b]) e = cudaFree(ctx->host_planes[b]);
+        ctx->host_planes[b] = nullptr;
+        ctx->host_planes_bytes[b] = 0;
+        if (e == cudaSuccess) e = cudaMalloc(&ctx->host_planes[b], need);
+        if (e != cudaSuccess) return cuda_fail(e, "render_host: device planes");
+        ctx->host_planes_bytes[b] = need;
+    }
+    cudaStream_t rs = ctx->host_stream, cs = ctx->host_copy_stream;
+    for (int32_t i = 0; i < n && e == cudaSuccess; ++i) {
+        const int b = i % nbuf;
+        const dqj_params &pi = p[i];
+        const dqj_outputs &ho = host_out[i];
+        const size_t px = (size_t)pi.width * (size_t)pi.height;
+        char *base = static_cast<char *>(ctx->host_planes[b]);
+        dqj_outputs dev{};
+        dev.pitch_px = pi.width;
+        dev.iter = ho.iter ? reinterpret_cast<int32_t *>(base) : nullptr;
+        dev.depth = ho.depth ? reinterpret_cast<float *>(base + px * 4) : nullptr;
+        dev.normal = ho.normal ? reinterpret_cast<float *>(base + px * 8) : nullptr;
+        dev.rgba = ho.rgba ? reinterpret_cast<uint8_t *>(base + px * 20) : nullptr;
+        dev.stats = ho.stats ? reinterpret_cast<int64_t *>(base + align_up(px * 24, 256)) : nullptr;
+        // the render into plane set b waits for that set's previous copy back
+        e = cudaStreamWaitEvent(rs, ctx->host_copied[b], 0);
+        if (e != cudaSuccess) break;
+        dqj_status s = enqueue_frame(ctx, pi, dev, rs);
+        if (s != DQJ_OK) {
+            cudaStreamSynchronize(cs);
+            return s;
+        }
+        e = cudaEventRecord(ctx->host_rendered[b], rs);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ctx->host_rendered[b], 0);
+        const size_t w = (size_t)pi.width, hp = (size_t)ho.pitch_px;
+        auto copy2d = [&](void *dst, const void *src, size_t elem) {
+            return cudaMemcpy2DAsync(dst, hp * elem, src, w * elem, w * elem, (size_t)pi.height,
+                                     cudaMemcpyDeviceToHost, cs);
+        };
+        if (e == cudaSuccess && ho.iter) e = copy2d(ho.iter, dev.iter, 4);
+        if (e == cudaSuccess && ho.depth) e = copy2d(ho.depth, dev.depth, 4);
+        if (e == cudaSuccess && ho.normal) e = copy2d(ho.normal, dev.normal, 12);
+        if (e == cudaSuccess && ho.rgba) e = copy2d(ho.rgba, dev.rgba, 4);
+        if (e == cudaSuccess && ho.stats)
+            e = cudaMemcpyAsync(ho.stats, dev.stats, DQJ_NSTATS * sizeof(int64_t), cudaMemcpyDeviceToHost, cs);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->host_copied[b], cs);
+    }
+    const cudaError_t e2 = cudaStreamSynchronize(cs);
+    if (e == cudaSuccess) e = e2;
     if (e != cudaSuccess) return cuda_fail(e, "render_host: copy back");
     return DQJ_OK;
+}
+
+dqj_status dqj_render_host(dqj_ctx *ctx, const dqj_params *p, const dqj_outputs *host_out)
+{
+    if (!p || !host_out) return fail(DQJ_ERR_INVALID, "params or outputs is NULL");
+    return dqj_render_host_batch(ctx, p, host_out, 1);
 }
 
 static void free_ring(dqj_ctx *ctx)

@@ -51,10 +51,13 @@ struct dqj_ctx {
     dqj::ScratchBuf scratch;
     cudaEvent_t done_ev = nullptr;   // last render's completion on its stream
     // dqj_render_host planes
-    cudaStream_t host_stream = nullptr;
-    void *host_planes = nullptr;
-    size_t host_planes_bytes = 0;
-    int64_t *host_stats_dev = nullptr;
+    // dqj_render_host / dqj_render_host_batch: two device plane sets, so that
+    // one frame's copy back overlaps the next frame's render
+    cudaStream_t host_stream = nullptr;       // renders
+    cudaStream_t host_copy_stream = nullptr;  // device -> host copies
+    void *host_planes[2] = {nullptr, nullptr};
+    size_t host_planes_bytes[2] = {0, 0};
+    cudaEvent_t host_rendered[2] = {nullptr, nullptr}, host_copied[2] = {nullptr, nullptr};
     // tile shapes chosen by the autotuner, keyed by (pixel-count class, iter bucket)
     std::map<int, std::pair<int, int>> tiles;
     std::mutex tiles_mu;             // guards tiles (read by the serving thread too)

@@ -719,10 +719,16 @@ dqj_status dqj_destroy(dqj_ctx *ctx)
         cudaSetDevice(ctx->device);
         if (ctx->done_ev) cudaEventSynchronize(ctx->done_ev);
         if (ctx->host_stream) cudaStreamSynchronize(ctx->host_stream);
+        if (ctx->host_copy_stream) cudaStreamSynchronize(ctx->host_copy_stream);
         scratch_free(ctx->scratch);
-        if (ctx->host_planes) cudaFree(ctx->host_planes);
+        for (int b = 0; b < 2; ++b) {
+            if (ctx->host_planes[b]) cudaFree(ctx->host_planes[b]);
+            if (ctx->host_rendered[b]) cudaEventDestroy(ctx->host_rendered[b]);
+            if (ctx->host_copied[b]) cudaEventDestroy(ctx->host_copied[b]);
+        }
         if (ctx->vox_scratch) cudaFree(ctx->vox_scratch);
         if (ctx->host_stream) cudaStreamDestroy(ctx->host_stream);
+        if (ctx->host_copy_stream) cudaStreamDestroy(ctx->host_copy_stream);
         if (ctx->done_ev) cudaEventDestroy(ctx->done_ev);
         for (auto &v : ctx->ev)
             if (v) cudaEventDestroy(v);

@@ -111,3 +111,17 @@ def test_de_rejects_recheck_precision(lib):
                                                  precision=scenes.PRECISION_FP32_RECHECK))
     assert lib.dqj_validate_params(binding.ctypes.byref(p)) == binding.DQJ_ERR_INVALID
     assert "DQJ_TRAVERSAL_DE" in binding.last_error()
+
+
+def test_render_host_batch_argument_errors():
+    ctx = binding.dqj_create(-1)
+    try:
+        with pytest.raises(binding.DqjError):
+            binding.dqj_render_host_batch(ctx, [scenes.default_scene()], [binding.make_outputs(pitch_px=256)])
+        assert "mock" in binding.last_error()
+        p = binding.make_params(scenes.default_scene())
+        o = binding.make_outputs(pitch_px=256)
+        assert binding.load().dqj_render_host_batch(binding.ctypes.c_void_p(ctx), binding.ctypes.byref(p),
+                                                    binding.ctypes.byref(o), -1) != binding.DQJ_OK
+    finally:
+        binding.dqj_destroy(ctx)

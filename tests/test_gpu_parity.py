@@ -187,3 +187,32 @@ def test_march_variants_bitwise_equal(rdr, scene, monkeypatch):
         for k in ("iter", "depth", "normal", "rgba"):
             assert np.array_equal(o[k], outs[0][k]), k
         assert o["stats"] == outs[0]["stats"]
+
+
+def test_render_host_batch_equals_device_render(rdr):
+    # host outputs through the double-buffered batch: every frame equals the
+    # device render of the same scene, with ragged sizes and a host pitch
+    import torch
+    frames = [scenes.default_scene(width=w, height=h, max_iter=mi)
+              for w, h, mi in ((96, 64, 12), (37, 19, 9), (128, 128, 16), (64, 48, 12), (1, 1, 5))]
+    host = []
+    for s in frames:
+        w, h = s["width"], s["height"]
+        pitch = w + 3
+        host.append({"iter": torch.full((h, pitch), -7, dtype=torch.int32).pin_memory(),
+                     "depth": torch.zeros((h, pitch), dtype=torch.float32).pin_memory(),
+                     "normal": torch.zeros((h, pitch, 3), dtype=torch.float32).pin_memory(),
+                     "rgba": torch.zeros((h, pitch, 4), dtype=torch.uint8).pin_memory(),
+                     "stats": torch.zeros(binding.DQJ_NSTATS, dtype=torch.int64).pin_memory(), "pitch_px": pitch})
+    binding.dqj_render_host_batch(rdr.ctx, frames, [binding.outputs_of(o) for o in host])
+    binding.dqj_render_host_batch(rdr.ctx, [], [])
+    for s, o in zip(frames, host):
+        ref = rdr.render(s)
+        w, h = s["width"], s["height"]
+        for k in ("iter", "depth", "normal", "rgba"):
+            assert np.array_equal(o[k][:, :w].numpy(), ref[k][:, :w].cpu().numpy()), k
+        assert np.all(o["iter"][:, w:].numpy() == -7)
+        assert binding.stats_dict(o["stats"]) == binding.stats_dict(ref["stats"])
+    bad = [frames[0], dict(frames[1], max_iter=0)]
+    with pytest.raises(binding.DqjError):
+        binding.dqj_render_host_batch(rdr.ctx, bad, [binding.outputs_of(o) for o in host[:2]])
