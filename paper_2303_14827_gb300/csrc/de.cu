@@ -8,9 +8,10 @@
 // and ends when no lane is active.  The derivative is carried squared,
 // |zeta'_{n+1}|^2 = 4 |zeta_n|^2 |zeta'_n|^2, so a step needs no square root;
 // the estimate 0.5 |zeta| / |zeta'| ln |zeta| = 0.25 sqrt(m / dr2) ln m is
-// formed once per sample from the modulus m and dr2 at the escape step.  (In
-// FP32 dr2 overflows only past ~21 steps, where the estimate is ~1e-15: an
-// overflow gives 0, which is below any epsilon, the same decision.)
+// formed once per sample from the modulus m and dr2 at the escape step, in
+// FP32 with the fast reciprocal square root and logarithm.  (In FP32 dr2
+// overflows only past ~21 steps, where the estimate is ~1e-15: an overflow
+// gives 0, which is below any epsilon, the same decision.)
 // Hits go to the hit list as (pixel, depth bits, n*); misses write their
 // planes directly.
 #include "render_common.cuh"
@@ -23,36 +24,57 @@ namespace {
 constexpr int kDeTileW = 8, kDeTileH = 4;
 
 // Lockstep classification with the squared derivative: returns the escape
-// count (0 = inside) and, for an escaped sample, the distance estimate.
-template <typename T, int SQ, int MOD>
+// count (0 = inside) and, for an escaped sample, the distance estimate.  AXIS:
+// only z[0..2] are set (the rest are zero) and the first step takes the axis
+// form (same results).
+template <typename T, int SQ, int MOD, bool AXIS>
 __device__ __forceinline__ int classify_de(T (&z)[8], const FrameT<T> &F, int max_iter, bool part, T &dist)
 {
     bool alive = part;
     int cnt = 0;
-    T sp = dq_sp<T>(z);
-    T m = modulus<T, MOD>(z);
-    T dr2 = T(1), m_esc = T(0), dr2_esc = T(1);
-    for (int n = 0; n < max_iter; ++n) {
-        dr2 = T(4) * m * dr2;
-        m = dq_iter<T, SQ, MOD>(z, z, sp, F.c);
-        const bool esc = alive && !(m <= F.R2);
-        if (esc) {
-            m_esc = m;
-            dr2_esc = dr2;
+    T sp, m;
+    if (AXIS) {
+        sp = dfma(z[2], z[2], z[1] * z[1]);
+        m = dfma(z[2], z[2], dfma(z[1], z[1], z[0] * z[0]));
+    } else {
+        sp = dq_sp<T>(z);
+        m = modulus<T, MOD>(z);
+    }
+    T dr2 = T(4) * m, m_esc = T(0), dr2_esc = T(1);
+    // the first step, peeled so that it can take the axis form
+    m = AXIS ? dq_iter_axis_first<T, MOD>(z, z, sp, F.c) : dq_iter<T, SQ, MOD>(z, z, sp, F.c);
+    if (alive && !(m <= F.R2)) {
+        m_esc = m;
+        dr2_esc = dr2;
+    }
+    alive = alive && (m <= F.R2);
+    cnt += alive ? 1 : 0;
+    if (__any_sync(kFull, alive)) {
+        for (int n = 1; n < max_iter; ++n) {
+            dr2 = T(4) * m * dr2;
+            m = dq_iter<T, SQ, MOD>(z, z, sp, F.c);
+            if (alive && !(m <= F.R2)) {
+                m_esc = m;
+                dr2_esc = dr2;
+            }
+            alive = alive && (m <= F.R2);
+            cnt += alive ? 1 : 0;
+            if (!__any_sync(kFull, alive)) break;
         }
-        alive = alive && (m <= F.R2);
-        cnt += alive ? 1 : 0;
-        if (!__any_sync(kFull, alive)) break;
     }
     if (!part || alive) {
         dist = T(0);
         return 0;
     }
-    dist = T(0.25) * sqrt(m_esc / dr2_esc) * log(m_esc);
+    // 0.5 |zeta| / |zeta'| ln |zeta| = 0.25 sqrt(m / dr2) ln m = 0.25 m / sqrt(m dr2) ln m
+    if constexpr (sizeof(T) == 4)
+        dist = 0.25f * m_esc * rsqrtf(m_esc * dr2_esc) * __logf(m_esc);  // fast forms in FP32
+    else
+        dist = T(0.25) * sqrt(m_esc / dr2_esc) * log(m_esc);
     return cnt + 1;
 }
 
-template <typename T, int SQ, int MOD>
+template <typename T, int SQ, int MOD, bool AXIS>
 __global__ void __launch_bounds__(kBlock) de_kernel(const __grid_constant__ FrameDesc fd, const Scratch sc)
 {
     const FrameT<T> &F = frame<T>(fd);
@@ -92,9 +114,9 @@ __global__ void __launch_bounds__(kBlock) de_kernel(const __grid_constant__ Fram
         while (__any_sync(kFull, act)) {
             T z[8];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) z[i] = dfma(t, D[i], F.A[i]);
+            for (int i = 0; i < (AXIS ? 3 : 8); ++i) z[i] = dfma(t, D[i], F.A[i]);  // AXIS: the rest are 0
             T dist;
-            const int n = classify_de<T, SQ, MOD>(z, F, fd.max_iter, act, dist);
+            const int n = classify_de<T, SQ, MOD, AXIS>(z, F, fd.max_iter, act, dist);
             if (act) {
                 ++steps;
                 st.iters += n ? (unsigned)n : (unsigned)fd.max_iter;
@@ -171,14 +193,17 @@ template <typename T, int SQ, int MOD>
 cudaError_t launch_de_t(const FrameDesc &fd, const Scratch &sc, cudaStream_t st, int num_sms, cudaEvent_t *ev)
 {
     static int g_de = 0, g_sh = 0;
-    if (!g_de) g_de = de_grid(de_kernel<T, SQ, MOD>, num_sms);
+    if (!g_de) g_de = de_grid(de_kernel<T, SQ, MOD, false>, num_sms);
     if (!g_sh) g_sh = de_grid(de_shade_kernel<T, SQ, MOD>, num_sms);
     const unsigned ntiles = (unsigned)((fd.W + kDeTileW - 1) / kDeTileW) * (unsigned)((fd.H + kDeTileH - 1) / kDeTileH);
     const int gd = (int)min((unsigned)g_de, (ntiles + 3u) / 4u);
     const unsigned maxw = ((unsigned)fd.W * (unsigned)fd.H + 31u) / 32u;
     const int gs = (int)min((unsigned)g_sh, (maxw + 3u) / 4u);
     if (ev) cudaEventRecord(ev[0], st);
-    de_kernel<T, SQ, MOD><<<gd > 0 ? gd : 1, kBlock, 0, st>>>(fd, sc);
+    if (fd.axis_slice)
+        de_kernel<T, SQ, MOD, true><<<gd > 0 ? gd : 1, kBlock, 0, st>>>(fd, sc);
+    else
+        de_kernel<T, SQ, MOD, false><<<gd > 0 ? gd : 1, kBlock, 0, st>>>(fd, sc);
     if (ev) cudaEventRecord(ev[1], st);
     de_shade_kernel<T, SQ, MOD><<<gs > 0 ? gs : 1, kBlock, 0, st>>>(fd, sc);
     if (ev) {

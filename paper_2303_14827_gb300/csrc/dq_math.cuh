@@ -131,6 +131,30 @@ __device__ __forceinline__ int classify_lockstep(T (&z)[8], const FrameT<T> &F, 
 
 // Scalar (per-thread) classification with early exit, for FP64 rechecks and
 // re-renders.  Same return convention.
+// Scalar form of dq_iter2_axis_first: the first step of a sample whose
+// components 3..7 are zero; same operations and order as dq_iter, so the same
+// result.  zi and z may be the same array.
+template <typename T, int MOD>
+__device__ __forceinline__ T dq_iter_axis_first(const T (&zi)[8], T (&z)[8], T &sp, const T (&c)[8])
+{
+    const T r0 = zi[0], r1 = zi[1], r2 = zi[2];
+    const T tr0 = r0 + r0;
+    z[0] = dfma(r0, r0, dfma(sp, T(-1), c[0]));
+    z[1] = dfma(tr0, r1, c[1]);
+    z[2] = dfma(tr0, r2, c[2]);
+#pragma unroll
+    for (int i = 3; i < 8; ++i) z[i] = c[i];
+    sp = dq_sp<T>(z);
+    T x = dfma(z[0], z[0], sp);
+    if (MOD == 0) {
+        x = dfma(z[4], z[4], x);
+        x = dfma(z[5], z[5], x);
+        x = dfma(z[6], z[6], x);
+        x = dfma(z[7], z[7], x);
+    }
+    return x;
+}
+
 template <typename T, int SQ, int MOD>
 __device__ __forceinline__ int classify_scalar(T (&z)[8], const FrameT<T> &F, int max_iter)
 {
