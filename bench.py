@@ -189,6 +189,24 @@ def oracle_sample_rate(target_s: float, seed: int = 11):
         n = int(min(W * H, n * max(2.0, 1.2 * target_s / max(dt, 1e-3))))
 
 
+def oracle_full_frames():
+    """The FP64 oracle on whole frames: the 256x256 single-frame scene on all
+    host cores and on one core, and one 1920x1080 workload frame (seed 0) on
+    all cores."""
+    import oracle
+    from paper_2303_14827_gb300 import scenes
+    out = {}
+    for name, s, threads in (("256x256_all_cores", scenes.default_scene(), 0),
+                             ("256x256_one_core", scenes.default_scene(), 1),
+                             ("1920x1080_seed0_all_cores", scenes.full_hd_scene(0), 0)):
+        t0 = time.perf_counter()
+        r = oracle.render(s, threads=threads)
+        dt = time.perf_counter() - t0
+        out[name] = {"seconds": round(dt, 3), "threads": r["threads"],
+                     "iters_per_s": (r["class_iters"] + r["normal_iters"]) / dt}
+    return out
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return 0
@@ -342,9 +360,11 @@ def run_gpu(args, world, rank, local):
         line["served"] = serving_section(local)
         line["batch64"] = batch_section(local)
 
+    line["c1"] = c1_section(local)
     if rank == 0 and not args.no_cpu_baseline:
         rate, _, cores, desc, _ = oracle_sample_rate(args.cpu_seconds)
-        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
+                                "full_frames": oracle_full_frames()}
 
     binding.dqj_destroy(ctx)
     if rank == 0:
@@ -516,6 +536,36 @@ def batch_section(local, n=64):
                 "served_over_plain": t_plain / t_served}
     finally:
         binding.dqj_destroy(ctx)
+
+
+def c1_section(local, reps=20):
+    """The 256x256 single-frame scene (max_iter 12, 256 march + 8 bisection
+    steps) on the GPU: ms per frame (CUDA events, mean over reps after a
+    warm-up), frames/s and DQ iterations/s."""
+    import torch
+
+    from paper_2303_14827_gb300 import binding, scenes
+    s = scenes.default_scene()
+    ctx = binding.dqj_create(local)
+    stream = torch.cuda.current_stream(local)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    o = binding.alloc_outputs(s["width"], s["height"], device=f"cuda:{local}")
+    try:
+        for _ in range(3):
+            binding.dqj_render(ctx, s, binding.outputs_of(o), stream.cuda_stream)
+        e0.record(stream)
+        for _ in range(reps):
+            binding.dqj_render(ctx, s, binding.outputs_of(o), stream.cuda_stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        st = binding.stats_dict(o["stats"])
+    finally:
+        binding.dqj_destroy(ctx)
+    it = st["class_iters"] + st["normal_iters"]
+    return {"workload": "256x256, c = (-0.2,0.6,0.2,0.2 | 0.1,0,0,0.05), max_iter 12, 256 march + 8 bisect, FP32",
+            "ms_per_frame": round(ms, 4), "frames_per_s": 1e3 / ms, "iters_per_frame": it,
+            "iters_per_s": it / (ms * 1e-3), "hits": st["hits"]}
 
 
 def precision_section(local, reps=3):
