@@ -184,20 +184,28 @@ __global__ void __launch_bounds__(kBlock) recheck_kernel(const __grid_constant__
     // a full queue: pixels whose samples did not fit were flagged by the pushers
 }
 
-// Full FP64 render of one pixel per thread (the reference sequence of steps).
+// Full FP64 render of one pixel per warp, with the oracle's formulas for the
+// sample positions (the reference sequence of steps).  The lanes classify 32
+// consecutive march samples at a time; a ballot finds the first inside one and
+// warp reductions give the largest escape count before it, so the result and
+// the iteration count are those of the sample-by-sample loop.  Bisection runs
+// on every lane alike; the six normal evaluations run on lanes 0..5.  Pixels go
+// to warps of different blocks first, so a short list spreads over the SMs.
 template <int SQ, int MOD>
 __global__ void __launch_bounds__(kBlock) fixup_kernel(const __grid_constant__ FrameDesc fd, const Scratch sc)
 {
     const FrameT<double> &F = fd.d;
+    const int lane = threadIdx.x & 31;
     const unsigned nd = min(*(volatile unsigned *)&sc.ctr->dirty_count, sc.dirty_cap);
+    const unsigned warp = (threadIdx.x >> 5) * gridDim.x + blockIdx.x, nwarps = gridDim.x * (blockDim.x >> 5);
     unsigned long long its = 0, npx = 0;
-    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < nd; i += gridDim.x * blockDim.x) {
+    for (unsigned i = warp; i < nd; i += nwarps) {
         const int pixel = sc.dirty_list[i];
         const int x = pixel % fd.W, y = pixel / fd.W;
-        npx += 1;
+        npx += lane == 0 ? 1 : 0;
         double d[3], t_in, t_out;
         if (!camera_clip<double>(F, fd.W, fd.H, x, y, d, t_in, t_out)) {
-            write_miss<double>(fd, x, y, 0);
+            if (lane == 0) write_miss<double>(fd, x, y, 0);
             continue;
         }
         const double delta = (t_out - t_in) / (double)fd.N;
@@ -207,22 +215,29 @@ __global__ void __launch_bounds__(kBlock) fixup_kernel(const __grid_constant__ F
             for (int j = 0; j < 8; ++j)
                 z[j] = F.O[j] + (F.eye[0] + t * d[0]) * F.E[0][j] + (F.eye[1] + t * d[1]) * F.E[1][j] +
                        (F.eye[2] + t * d[2]) * F.E[2][j];
-            const int n = classify_scalar<double, SQ, MOD>(z, F, fd.max_iter);
-            its += n ? n : fd.max_iter;
-            return n;
+            return classify_scalar<double, SQ, MOD>(z, F, fd.max_iter);
         };
         int esc_max = 0, n_prev = 0, k_first = -1;
-        for (int k = 0; k <= fd.N; ++k) {
-            const int n = cls(t_in + (double)k * delta);
-            if (n == 0) {
-                k_first = k;
+        for (int k0 = 0; k0 <= fd.N; k0 += 32) {
+            const int k = k0 + lane;
+            const bool part = k <= fd.N;
+            const int n = part ? cls(t_in + (double)k * delta) : 1;
+            const unsigned inside = __ballot_sync(kFull, part && n == 0);
+            const int first = inside ? __ffs(inside) - 1 : 32;  // samples before it escaped
+            if (part && lane <= first) its += n ? (unsigned)n : (unsigned)fd.max_iter;
+            int m = part && lane < first ? n : 0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(kFull, m, o));
+            esc_max = max(esc_max, m);
+            if (inside) {
+                if (first > 0) n_prev = __shfl_sync(kFull, n, first - 1);  // else: last of the previous chunk
+                k_first = k0 + first;
                 break;
             }
-            esc_max = n > esc_max ? n : esc_max;
-            n_prev = n;
+            n_prev = __shfl_sync(kFull, n, 31);
         }
         if (k_first < 0) {
-            write_miss<double>(fd, x, y, esc_max);
+            if (lane == 0) write_miss<double>(fd, x, y, esc_max);
             continue;
         }
         double depth = t_in;
@@ -233,6 +248,7 @@ __global__ void __launch_bounds__(kBlock) fixup_kernel(const __grid_constant__ F
             for (int b = 0; b < fd.B; ++b) {
                 const double mid = lo + 0.5 * (hi - lo);
                 const int n = cls(mid);
+                if (lane == 0) its += n ? (unsigned)n : (unsigned)fd.max_iter;
                 if (n == 0) {
                     hi = mid;
                 } else {
@@ -242,27 +258,28 @@ __global__ void __launch_bounds__(kBlock) fixup_kernel(const __grid_constant__ F
             }
             depth = lo + 0.5 * (hi - lo);
         }
-        double g[3];
-        bool guard = false;
-        for (int a = 0; a < 3; ++a) {
-            double fv[2];
-            for (int s = 0; s < 2; ++s) {
-                double p[3] = {F.eye[0] + depth * d[0], F.eye[1] + depth * d[1], F.eye[2] + depth * d[2]};
-                p[a] += s == 0 ? F.h : -F.h;
-                double z[8];
-                for (int j = 0; j < 8; ++j) z[j] = F.O[j] + p[0] * F.E[0][j] + p[1] * F.E[1][j] + p[2] * F.E[2][j];
-                double sp = dq_sp<double>(z);
-                for (int n = 0; n < n_star; ++n) dq_iter<double, SQ, MOD>(z, z, sp, F.c);
-                its += n_star;
-                fv[s] = modulus<double, MOD>(z);
-                guard = guard || !(fv[s] <= normal_fmax(0.0));
-            }
-            g[a] = fv[0] - fv[1];
+        // normal: lane 2a + s evaluates F at p +- h e_a
+        double fv = 0.0;
+        if (lane < 6) {
+            const int a = lane >> 1;
+            double p[3] = {F.eye[0] + depth * d[0], F.eye[1] + depth * d[1], F.eye[2] + depth * d[2]};
+            p[a] += (lane & 1) == 0 ? F.h : -F.h;
+            double z[8];
+            for (int j = 0; j < 8; ++j) z[j] = F.O[j] + p[0] * F.E[0][j] + p[1] * F.E[1][j] + p[2] * F.E[2][j];
+            double sp = dq_sp<double>(z);
+            for (int n = 0; n < n_star; ++n) dq_iter<double, SQ, MOD>(z, z, sp, F.c);
+            its += (unsigned)n_star;
+            fv = modulus<double, MOD>(z);
         }
-        shade_write<double>(fd, F, x, y, n_star, depth, g, guard, d);
+        const bool bad = lane < 6 && !(fv <= normal_fmax(0.0));
+        const bool guard = __any_sync(kFull, bad);
+        double g[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) g[a] = __shfl_sync(kFull, fv, 2 * a) - __shfl_sync(kFull, fv, 2 * a + 1);
+        if (lane == 0) shade_write<double>(fd, F, x, y, n_star, depth, g, guard, d);
     }
-    unsigned long long v = warp_sum(its), p = warp_sum(npx);
-    if ((threadIdx.x & 31) == 0) {
+    const unsigned long long v = warp_sum(its), p = warp_sum(npx);
+    if (lane == 0) {
         if (v) atomicAdd(&sc.ctr->stats[6], v);
         if (p) atomicAdd(&sc.ctr->stats[5], p);
     }
