@@ -155,6 +155,21 @@ __device__ __forceinline__ T dq_iter_axis_first(const T (&zi)[8], T (&z)[8], T &
     return x;
 }
 
+// classify_scalar that also reports whether any tested modulus, up to and
+// including the escaping one, lay within F.margin of R^2.
+template <typename T, int SQ, int MOD>
+__device__ __forceinline__ int classify_scalar_margin(T (&z)[8], const FrameT<T> &F, int max_iter, bool &marginal)
+{
+    T sp = dq_sp<T>(z);
+    marginal = false;
+    for (int n = 1; n <= max_iter; ++n) {
+        const T m = dq_iter<T, SQ, MOD>(z, z, sp, F.c);
+        marginal = marginal || fabs(m - F.R2) <= F.margin;
+        if (m > F.R2) return n;
+    }
+    return 0;
+}
+
 template <typename T, int SQ, int MOD>
 __device__ __forceinline__ int classify_scalar(T (&z)[8], const FrameT<T> &F, int max_iter)
 {

@@ -184,8 +184,10 @@ __global__ void __launch_bounds__(kBlock) recheck_kernel(const __grid_constant__
     // a full queue: pixels whose samples did not fit were flagged by the pushers
 }
 
-// Full FP64 render of one pixel per warp, with the oracle's formulas for the
-// sample positions (the reference sequence of steps).  The lanes classify 32
+// Re-render of one pixel per warp, with the oracle's formulas for the sample
+// positions (the reference sequence of steps) in FP64; a march sample is
+// classified in FP32 and again in FP64 only when it is marginal; bisection
+// (five levels per round across the lanes) and normals are FP64.  The lanes classify 32
 // consecutive march samples at a time; a ballot finds the first inside one and
 // warp reductions give the largest escape count before it, so the result and
 // the iteration count are those of the sample-by-sample loop.  Bisection runs
@@ -209,19 +211,35 @@ __global__ void __launch_bounds__(kBlock) fixup_kernel(const __grid_constant__ F
             continue;
         }
         const double delta = (t_out - t_in) / (double)fd.N;
-        auto cls = [&](double t) {
-            double z[8];
+        auto slice = [&](double t, double (&z)[8]) {
 #pragma unroll
             for (int j = 0; j < 8; ++j)
                 z[j] = F.O[j] + (F.eye[0] + t * d[0]) * F.E[0][j] + (F.eye[1] + t * d[1]) * F.E[1][j] +
                        (F.eye[2] + t * d[2]) * F.E[2][j];
+        };
+        auto cls = [&](double t) {
+            double z[8];
+            slice(t, z);
             return classify_scalar<double, SQ, MOD>(z, F, fd.max_iter);
+        };
+        // a march sample: FP32 first, FP64 only when some FP32 modulus came within
+        // the recheck margin of R^2 (the premise of the recheck mode: outside the
+        // margin FP32 decides as FP64 does)
+        auto cls_march = [&](double t) {
+            double z[8];
+            slice(t, z);
+            float zf[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) zf[j] = (float)z[j];
+            bool marginal;
+            const int n32 = classify_scalar_margin<float, SQ, MOD>(zf, fd.f, fd.max_iter, marginal);
+            return marginal ? classify_scalar<double, SQ, MOD>(z, F, fd.max_iter) : n32;
         };
         int esc_max = 0, n_prev = 0, k_first = -1;
         for (int k0 = 0; k0 <= fd.N; k0 += 32) {
             const int k = k0 + lane;
             const bool part = k <= fd.N;
-            const int n = part ? cls(t_in + (double)k * delta) : 1;
+            const int n = part ? cls_march(t_in + (double)k * delta) : 1;
             const unsigned inside = __ballot_sync(kFull, part && n == 0);
             const int first = inside ? __ffs(inside) - 1 : 32;  // samples before it escaped
             if (part && lane <= first) its += n ? (unsigned)n : (unsigned)fd.max_iter;
@@ -245,15 +263,40 @@ __global__ void __launch_bounds__(kBlock) fixup_kernel(const __grid_constant__ F
         if (k_first > 0) {
             double lo = t_in + (double)(k_first - 1) * delta, hi = t_in + (double)k_first * delta;
             n_star = n_prev;
-            for (int b = 0; b < fd.B; ++b) {
-                const double mid = lo + 0.5 * (hi - lo);
-                const int n = cls(mid);
-                if (lane == 0) its += n ? (unsigned)n : (unsigned)fd.max_iter;
-                if (n == 0) {
-                    hi = mid;
-                } else {
-                    lo = mid;
-                    n_star = n;
+            // Bisection, up to five levels per round: lane j - 1 holds node j of the
+            // level tree (node 1 the next midpoint, children 2j: inside -> [lo, mid],
+            // 2j + 1: outside -> [mid, hi]), derives its interval with the same
+            // operations as the sequential halvings and classifies its midpoint;
+            // the path is then replayed, so the bracket is the sequential one.
+            for (int b0 = 0; b0 < fd.B; b0 += 5) {
+                const int levels = min(5, fd.B - b0);
+                const int node = lane + 1;
+                const int depth_j = 31 - __clz(node);  // level of the node
+                int n = 1;
+                if (depth_j < levels) {
+                    double l = lo, h = hi;
+                    for (int q = depth_j - 1; q >= 0; --q) {  // path bits below the leading one
+                        const double mid = l + 0.5 * (h - l);
+                        if ((node >> q) & 1)
+                            l = mid;
+                        else
+                            h = mid;
+                    }
+                    n = cls(l + 0.5 * (h - l));
+                }
+                int cur = 1;
+                for (int q = 0; q < levels; ++q) {
+                    const int nq = __shfl_sync(kFull, n, cur - 1);
+                    const double mid = lo + 0.5 * (hi - lo);
+                    if (lane == 0) its += nq ? (unsigned)nq : (unsigned)fd.max_iter;
+                    if (nq == 0) {
+                        hi = mid;
+                        cur = 2 * cur;
+                    } else {
+                        lo = mid;
+                        n_star = nq;
+                        cur = 2 * cur + 1;
+                    }
                 }
             }
             depth = lo + 0.5 * (hi - lo);
