@@ -194,7 +194,15 @@ dqj_status dqj_create(const dqj_config *cfg, dqj_ctx **out);
 
 /* Enqueue one frame on cuda_stream (a cudaStream_t; NULL = legacy default) and
  * return without waiting.  Outputs are caller-owned device memory.  Renders on one
- * context are ordered with each other across streams (they share scratch). */
+ * context are ordered with each other across streams (they share scratch).
+ * Stream capture (CUDA graphs): a render may be captured once the context has
+ * rendered a frame at least as large (with the same precision class), since a
+ * captured render neither allocates nor synchronizes (DQJ_ERR_INVALID
+ * otherwise).  Renders captured together are ordered with each other; the
+ * caller orders the capture after the context's earlier work (e.g. by
+ * synchronizing first), replays of graphs holding renders of one context
+ * must not overlap each other or other renders on it, and such graphs are
+ * destroyed before the context (they use its events and scratch memory). */
 dqj_status dqj_render(dqj_ctx *ctx, const dqj_params *p, const dqj_outputs *out, void *cuda_stream);
 
 /* Render one frame into HOST buffers: the library renders into context-owned

@@ -286,17 +286,45 @@ static dqj_status enqueue_frame(dqj_ctx *ctx, const dqj_params &p, const dqj_out
     fd.normal = out.normal;
     fd.rgba = out.rgba;
     const uint64_t px = (uint64_t)p.width * (uint64_t)p.height;
-    dqj_status s = scratch_ensure(ctx->scratch, px, p.precision == DQJ_FP32_RECHECK);
-    if (s != DQJ_OK) return s;
+    // Under stream capture (a CUDA graph) nothing may allocate or synchronize, a
+    // wait on an event recorded outside the capture is not allowed, and a
+    // replay repeats the frame's constants, so the per-pixel tags of the
+    // recheck mode are cleared by the frame itself instead of changing epoch.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    unsigned long long cap_id = 0;
+    // launch errors are read back with cudaGetLastError: start from a clean
+    // slate, so an earlier failed call of the caller's is not taken for ours
+    (void)cudaGetLastError();
+    cudaError_t e = cudaStreamGetCaptureInfo(st, &cap, &cap_id);
+    if (e != cudaSuccess) return cuda_fail(e, "render: cudaStreamGetCaptureInfo");
+    const bool capturing = cap == cudaStreamCaptureStatusActive;
+    const bool recheck = p.precision == DQJ_FP32_RECHECK;
     ScratchBuf &sb = ctx->scratch;
-    if (++sb.epoch == 0) {  // tags wrapped: clear the per-pixel flags
-        cudaError_t e = cudaMemsetAsync(sb.view.dirty_flag, 0, (size_t)sb.pixels * sizeof(uint32_t), st);
-        if (e != cudaSuccess) return cuda_fail(e, "render: clear flags");
-        sb.epoch = 1;
+    if (capturing && !(sb.base && px <= sb.pixels && (!recheck || sb.with_queue)))
+        return fail(DQJ_ERR_INVALID, "render: under stream capture the context's scratch must already fit the frame "
+                                     "(render the largest frame once before capturing)");
+    dqj_status s = scratch_ensure(sb, px, recheck);
+    if (s != DQJ_OK) return s;
+    if (capturing) {
+        if (recheck) {
+            e = cudaMemsetAsync(sb.view.dirty_flag, 0, (size_t)sb.pixels * sizeof(uint32_t), st);
+            if (e != cudaSuccess) return cuda_fail(e, "render: clear flags");
+        }
+        fd.epoch = 1;
+    } else {
+        if (++sb.epoch == 0) {  // tags wrapped: clear the per-pixel flags
+            e = cudaMemsetAsync(sb.view.dirty_flag, 0, (size_t)sb.pixels * sizeof(uint32_t), st);
+            if (e != cudaSuccess) return cuda_fail(e, "render: clear flags");
+            sb.epoch = 1;
+        }
+        fd.epoch = sb.epoch;
     }
-    fd.epoch = sb.epoch;
-    cudaError_t e = cudaStreamWaitEvent(st, ctx->done_ev, 0);
-    if (e != cudaSuccess) return cuda_fail(e, "render: cudaStreamWaitEvent");
+    // the previous render's event: waited on only when it was recorded in the
+    // same capture state (a record inside a graph is ordered by its replays)
+    if (ctx->done_capture == (capturing ? cap_id : 0ull)) {
+        e = cudaStreamWaitEvent(st, ctx->done_ev, 0);
+        if (e != cudaSuccess) return cuda_fail(e, "render: cudaStreamWaitEvent");
+    }
     e = cudaMemsetAsync(sb.view.ctr, 0, sizeof(Counters), st);
     if (e != cudaSuccess) return cuda_fail(e, "render: clear counters");
     cudaEvent_t *ev = nullptr;
@@ -309,6 +337,7 @@ static dqj_status enqueue_frame(dqj_ctx *ctx, const dqj_params &p, const dqj_out
     }
     e = cudaEventRecord(ctx->done_ev, st);
     if (e != cudaSuccess) return cuda_fail(e, "render: cudaEventRecord");
+    ctx->done_capture = capturing ? cap_id : 0;
     return DQJ_OK;
 }
 

@@ -50,6 +50,7 @@ struct dqj_ctx {
     std::mutex mu;                   // orders renders on this context
     dqj::ScratchBuf scratch;
     cudaEvent_t done_ev = nullptr;   // last render's completion on its stream
+    unsigned long long done_capture = 0;  // stream-capture id done_ev was last recorded under (0: none)
     // dqj_render_host planes
     // dqj_render_host / dqj_render_host_batch: two device plane sets, so that
     // one frame's copy back overlaps the next frame's render

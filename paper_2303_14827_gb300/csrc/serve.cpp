@@ -688,6 +688,7 @@ dqj_status dqj_poll(dqj_ctx *ctx, dqj_ticket ticket, int *done, dqj_status *resu
 dqj_status dqj_destroy(dqj_ctx *ctx)
 {
     if (!ctx) return fail(DQJ_ERR_INVALID, "ctx is NULL");
+    const bool device_ctx = ctx->device != DQJ_DEVICE_MOCK;
     dqj_status result = DQJ_OK;
     if (ctx->serve) {
         ServeState &S = *ctx->serve;
@@ -717,7 +718,10 @@ dqj_status dqj_destroy(dqj_ctx *ctx)
     }
     if (ctx->device != DQJ_DEVICE_MOCK) {
         cudaSetDevice(ctx->device);
-        if (ctx->done_ev) cudaEventSynchronize(ctx->done_ev);
+        if (ctx->done_capture)  // the last render was captured in a graph: its event is a graph node
+            cudaDeviceSynchronize();
+        else if (ctx->done_ev)
+            cudaEventSynchronize(ctx->done_ev);
         if (ctx->host_stream) cudaStreamSynchronize(ctx->host_stream);
         if (ctx->host_copy_stream) cudaStreamSynchronize(ctx->host_copy_stream);
         scratch_free(ctx->scratch);
@@ -735,6 +739,7 @@ dqj_status dqj_destroy(dqj_ctx *ctx)
         ctx->ev.clear();
     }
     delete ctx;
+    if (device_ctx) (void)cudaGetLastError();  // teardown leaves no error behind for the caller
     return result;
 }
 
