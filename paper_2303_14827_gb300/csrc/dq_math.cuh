@@ -237,9 +237,11 @@ __device__ __forceinline__ float2 dq_iter2(const float2 (&zi)[8], float2 (&z)[8]
 // components 3..7 of the input are zero (the slice origin and basis vanish
 // there), so every product with them is zero and the step reduces to the terms
 // below.  The operations kept are those of dq_iter2 in the same order, so the
-// result is the same (up to the sign of zero components, which no later modulus
-// or comparison sees).  Both squaring modes give the same step here.
-template <int MOD>
+// iterate is the same (up to the sign of zero components, which no later
+// modulus or comparison sees).  Both squaring modes give the same step here.
+// Returns a = z0^2 + sp only: the rest of the modulus adds the fixed c4..c7
+// terms, and the step's tests use the thresholds on a in P (t_esc, t_mlo,
+// t_mhi), which decide exactly as the full modulus would.
 __device__ __forceinline__ float2 dq_iter2_axis_first(const float2 (&zi)[8], float2 (&z)[8], float2 &sp,
                                                       const PairConsts &P)
 {
@@ -251,14 +253,7 @@ __device__ __forceinline__ float2 dq_iter2_axis_first(const float2 (&zi)[8], flo
 #pragma unroll
     for (int i = 3; i < 8; ++i) z[i] = P.c[i];
     sp = f2fma(z[3], z[3], f2fma(z[2], z[2], f2mul(z[1], z[1])));
-    float2 x = f2fma(z[0], z[0], sp);
-    if (MOD == 0) {
-        x = f2fma(z[4], z[4], x);
-        x = f2fma(z[5], z[5], x);
-        x = f2fma(z[6], z[6], x);
-        x = f2fma(z[7], z[7], x);
-    }
-    return x;
+    return f2fma(z[0], z[0], sp);
 }
 
 // Lockstep classification of two samples per lane (halves .x and .y), same
@@ -279,17 +274,17 @@ __device__ __forceinline__ void classify_lockstep2(float2 (&z)[8], const PairCon
     int n0 = 0;
     if constexpr (AXIS) {  // the first trip, peeled so that its first step takes the axis form
         n0 = max_iter;
-        float2 x = dq_iter2_axis_first<MOD>(z, w, sp, P);
+        const float2 a = dq_iter2_axis_first(z, w, sp, P);  // thresholds on a, exact (see PairConsts)
         if (RECHECK) {
-            ma = ma || (aa && fabsf(x.x - R2) <= margin);
-            mb = mb || (ab && fabsf(x.y - R2) <= margin);
+            ma = ma || (aa && a.x >= P.t_mlo && a.x <= P.t_mhi);
+            mb = mb || (ab && a.y >= P.t_mlo && a.y <= P.t_mhi);
         }
-        aa = aa && (x.x <= R2);
-        ab = ab && (x.y <= R2);
+        aa = aa && (a.x < P.t_esc);
+        ab = ab && (a.y < P.t_esc);
         na += aa ? 1 : 0;
         nb += ab ? 1 : 0;
         if (__any_sync(0xffffffffu, aa || ab) && max_iter > 1) {
-            x = dq_iter2<SQ, MOD>(w, z, sp, P);
+            float2 x = dq_iter2<SQ, MOD>(w, z, sp, P);
             if (RECHECK) {
                 ma = ma || (aa && fabsf(x.x - R2) <= margin);
                 mb = mb || (ab && fabsf(x.y - R2) <= margin);

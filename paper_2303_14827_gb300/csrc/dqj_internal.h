@@ -44,6 +44,11 @@ struct PairConsts {
     float2 c[8];
     float2 A[8];
     float2 neg1, neg2;
+    // Axis-slice first step: its modulus is a = z0^2 + sp followed by the fixed
+    // FMAs with c4..c7 (EUCLID8), a monotone function of a, so its tests are
+    // thresholds on a, found on the host: escape <=> a >= t_esc; recheck margin
+    // <=> t_mlo <= a <= t_mhi.
+    float t_esc, t_mlo, t_mhi, t_pad;
 };
 
 struct alignas(16) FrameDesc {

@@ -109,6 +109,64 @@ static void cast_frame(const FrameT<double> &d, FrameT<T> &f)
     for (size_t i = 0; i < sizeof(FrameT<double>) / sizeof(double); ++i) dst[i] = (T)src[i];
 }
 
+// The modulus after the axis-slice first step, as the device forms it from the
+// partial sum a = z0^2 + sp: EUCLID8 adds c4^2 .. c7^2 by four rounded FMAs
+// (every component 3..7 equals c there), DUALNUM adds nothing.
+static float axis_first_modulus(float a, const FrameT<float> &F, int modulus_mode)
+{
+    if (modulus_mode == 0)
+        for (int i = 4; i < 8; ++i) a = std::fmaf(F.c[i], F.c[i], a);
+    return a;
+}
+
+// Smallest non-negative float (by bit pattern, which orders them) for which a
+// monotone false -> true predicate holds; 0x7f800001 when none does.
+template <typename Pred>
+static uint32_t first_true(Pred pred)
+{
+    auto as_f = [](uint32_t b) {
+        float f;
+        std::memcpy(&f, &b, sizeof f);
+        return f;
+    };
+    uint32_t lo = 0, hi = 0x7f800000u;  // +0 .. +inf
+    if (!pred(as_f(hi))) return 0x7f800001u;
+    while (lo < hi) {
+        const uint32_t mid = lo + (hi - lo) / 2;
+        if (pred(as_f(mid)))
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    return lo;
+}
+
+// Thresholds of the axis-slice first step on a = z0^2 + sp >= 0: every rounded
+// FMA is non-decreasing in a, so "modulus > R^2" holds exactly from t_esc up,
+// and "|modulus - R^2| <= margin" (the recheck test, in FP32 as the device
+// forms it) exactly on [t_mlo, t_mhi] (empty when t_mlo > t_mhi).
+void axis_first_thresholds(const FrameT<float> &F, int modulus_mode, PairConsts &P)
+{
+    auto bits_f = [](uint32_t b) {
+        float f;
+        std::memcpy(&f, &b, sizeof f);
+        return f;
+    };
+    const float R2 = F.R2, margin = F.margin;
+    auto x = [&](float a) { return axis_first_modulus(a, F, modulus_mode); };
+    P.t_esc = bits_f(first_true([&](float a) { return x(a) > R2; }));
+    const uint32_t lo = first_true([&](float a) { return x(a) - R2 >= -margin; });
+    const uint32_t above = first_true([&](float a) { return x(a) - R2 > margin; });
+    if (lo > 0x7f800000u || above == 0 || above <= lo) {
+        P.t_mlo = INFINITY;
+        P.t_mhi = -1.f;
+    } else {
+        P.t_mlo = bits_f(lo);
+        P.t_mhi = bits_f(above - 1);
+    }
+    P.t_pad = 0.f;
+}
+
 void derive_frame(const dqj_params &p, FrameDesc &fd, int tile_w, int tile_h)
 {
     std::memset(&fd, 0, sizeof fd);
@@ -173,6 +231,7 @@ void derive_frame(const dqj_params &p, FrameDesc &fd, int tile_w, int tile_h)
     }
     fd.p2.neg1 = make_float2(-1.f, -1.f);
     fd.p2.neg2 = make_float2(-2.f, -2.f);
+    axis_first_thresholds(fd.f, p.modulus_mode, fd.p2);
     fd.W = p.width;
     fd.H = p.height;
     fd.max_iter = p.max_iter;

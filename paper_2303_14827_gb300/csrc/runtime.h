@@ -23,6 +23,8 @@ dqj_status cuda_fail(cudaError_t e, const char *what);
 // Validation and derivation of the per-frame constants (host, double).
 dqj_status validate(const dqj_params *p);
 void derive_frame(const dqj_params &p, FrameDesc &fd, int tile_w, int tile_h);
+// Exact thresholds of the axis-slice first step's tests (see PairConsts).
+void axis_first_thresholds(const FrameT<float> &F, int modulus_mode, PairConsts &P);
 
 // Scratch block sized for a pixel count; grow-only.
 struct ScratchBuf {
