@@ -13,10 +13,11 @@
  *   - the 8-D space is cut by a 3-D slice, five coordinates held fixed
  *     (Method, "Dimension Reduction");
  *   - each pixel's ray is marched through a bounding box, the first inside
- *     sample refined by bisection (Method, "Ray-Marching"); a normal comes from
- *     central differences of neighbouring samples (Method,
- *     "Lighting/Illumination") and is shaded with the ambient and diffuse terms
- *     of Eq. phong.
+ *     sample refined by bisection, or sphere-traced by the distance estimate of
+ *     Eq. distfract2 (Method, "Ray-Marching"); a normal comes from central
+ *     differences of neighbouring samples (Method, "Lighting/Illumination")
+ *     and is shaded with the ambient and diffuse terms of Eq. phong, and its
+ *     specular term when k_specular > 0.
  *
  * All functions return a dqj_status; no C++ exception crosses this boundary.
  * On a non-OK status, dqj_last_error() returns a message for the calling thread.
@@ -148,6 +149,8 @@ typedef struct {
  *          the first march sample is inside); miss: largest escape count over
  *          the march samples (0 when the ray misses the box)
  *   depth  ray parameter of the hit (midpoint of the final bracket), +inf on miss
+ *          (DQJ_TRAVERSAL_DE: the hit sample's t and escape count, see
+ *          dqj_params.traversal)
  *   normal unit normal (+gradient of the modulus field), (0,0,0) on miss
  *   rgba   shaded colour, alpha 255 on hit; (0,0,0,0) on miss
  *   stats  optional DEVICE (render) / HOST (render_host) array of DQJ_NSTATS
@@ -164,10 +167,10 @@ typedef struct {
 
 /* Indices into dqj_outputs.stats. */
 enum {
-    DQJ_STAT_CLASS_ITERS = 0,  /* DQ iterations of march + bisection samples          */
+    DQJ_STAT_CLASS_ITERS = 0,  /* DQ iterations of march + bisection (or DE) samples  */
     DQJ_STAT_NORMAL_ITERS = 1, /* DQ iterations of the six normal evaluations         */
-    DQJ_STAT_SAMPLES = 2,      /* classified samples (march + bisection)              */
-    DQJ_STAT_HITS = 3,         /* pixels with an inside march sample                  */
+    DQJ_STAT_SAMPLES = 2,      /* classified samples (march + bisection, or DE)       */
+    DQJ_STAT_HITS = 3,         /* hit pixels                                          */
     DQJ_STAT_RECHECKS = 4,     /* samples re-evaluated in FP64                        */
     DQJ_STAT_FIXUPS = 5,       /* pixels re-rendered in FP64 after a disagreement     */
     DQJ_STAT_FIXUP_ITERS = 6,  /* DQ iterations spent by those re-renders             */
@@ -181,7 +184,9 @@ enum {
  * 0.1, 0, 0, 0.05), real-quaternion coordinates 0..2 free, 256x256, max_iter 12,
  * R = 4, N = 256, B = 8, h = 1e-4, box [-2,2]^3, eye (0,0,3.5) looking at the
  * origin, up +y, fov 45, light (1,1,1), k_a 0.15, k_d 0.85, white albedo,
- * DQJ_FP32, margin 1e-3, algebraic square, EUCLID8 modulus. */
+ * DQJ_FP32, margin 1e-3, algebraic square, EUCLID8 modulus, no specular term
+ * (k_s 0, s 32), DQJ_TRAVERSAL_MARCH (DE fields: 512 steps, epsilon 1e-3,
+ * scale 1, no bounding sphere). */
 dqj_status dqj_default_params(dqj_params *p);
 
 /* Check a parameter block on the host (no device needed).  DQJ_ERR_INVALID
@@ -310,8 +315,8 @@ dqj_status dqj_voxelize(dqj_ctx *ctx, const dqj_params *p, int32_t grid_n, uint8
 #define DQJ_NOALLOC_MAX_PIXELS 262144u
 
 /*
- * dqj_render_noalloc -- the plain render without any device allocation.  (An
- * interface of this library; the paper has no counterpart.)
+ * dqj_render_noalloc -- the plain render (either traversal) without any device
+ * allocation.  (An interface of this library; the paper has no counterpart.)
  *
  * For callers that must not allocate device memory.  Examples: a host
  * application that reserves all device memory for its own pool before loading
@@ -337,9 +342,12 @@ dqj_status dqj_render_noalloc(const dqj_params *p, const dqj_outputs *out, void 
 /* Message for the last non-OK status on this thread ("" if none). */
 const char *dqj_last_error(void);
 
-/* Measurement: FP32 FMA throughput of this GPU with independent dependency
- * chains.  variant 0 = scalar fma.rn.f32, 1 = paired fma.rn.f32x2.  Runs
- * `launches` timed launches on device `device`; *flops_per_s gets the best. */
+/* Measurement: FMA throughput of this GPU with independent dependency chains
+ * (the roofline denominator of the renderer).  variant 0 = scalar fma.rn.f32,
+ * 1 = paired fma.rn.f32x2, 2 / 3 = as 0 / 1 with two integer operations per
+ * eight FMAs, 4 = fma.rn.f64; only FMAs count as flops.  Runs `launches` timed
+ * launches on device `device`; *flops_per_s gets the best.  An interface of
+ * this library; the paper has no counterpart. */
 dqj_status dqj_fma_peak(int32_t device, int32_t variant, int32_t launches, double *flops_per_s);
 
 #ifdef __cplusplus
