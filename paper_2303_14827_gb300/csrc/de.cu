@@ -180,25 +180,16 @@ __global__ void __launch_bounds__(kBlock) de_shade_kernel(const __grid_constant_
     flush_stat(&sc.ctr->stats[1], st.niters);
 }
 
-template <typename K>
-int de_grid(K kernel, int num_sms)
-{
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, 0) != cudaSuccess || per_sm < 1)
-        per_sm = 1;
-    return per_sm * num_sms;
-}
-
 template <typename T, int SQ, int MOD>
 cudaError_t launch_de_t(const FrameDesc &fd, const Scratch &sc, cudaStream_t st, int num_sms, cudaEvent_t *ev)
 {
-    static int g_de = 0, g_sh = 0;
-    if (!g_de) g_de = de_grid(de_kernel<T, SQ, MOD, false>, num_sms);
-    if (!g_sh) g_sh = de_grid(de_shade_kernel<T, SQ, MOD>, num_sms);
+    static std::atomic<int> g_de{0}, g_sh{0};
+    const int cap_de = num_sms * resident_per_sm(g_de, de_kernel<T, SQ, MOD, false>);
+    const int cap_sh = num_sms * resident_per_sm(g_sh, de_shade_kernel<T, SQ, MOD>);
     const unsigned ntiles = (unsigned)((fd.W + kDeTileW - 1) / kDeTileW) * (unsigned)((fd.H + kDeTileH - 1) / kDeTileH);
-    const int gd = (int)min((unsigned)g_de, (ntiles + 3u) / 4u);
+    const int gd = (int)min((unsigned)cap_de, (ntiles + 3u) / 4u);
     const unsigned maxw = ((unsigned)fd.W * (unsigned)fd.H + 31u) / 32u;
-    const int gs = (int)min((unsigned)g_sh, (maxw + 3u) / 4u);
+    const int gs = (int)min((unsigned)cap_sh, (maxw + 3u) / 4u);
     if (ev) cudaEventRecord(ev[0], st);
     if (fd.axis_slice)
         de_kernel<T, SQ, MOD, true><<<gd > 0 ? gd : 1, kBlock, 0, st>>>(fd, sc);

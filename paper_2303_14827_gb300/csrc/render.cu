@@ -328,25 +328,16 @@ __global__ void __launch_bounds__(kBlock) fixup_kernel(const __grid_constant__ F
     }
 }
 
-template <typename K>
-int persistent_grid(K kernel, int num_sms)
-{
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, 0) != cudaSuccess || per_sm < 1)
-        per_sm = 1;
-    return per_sm * num_sms;
-}
-
 template <typename T, int SQ, int MOD, bool RECHECK>
 cudaError_t launch_passes(const FrameDesc &fd, const Scratch &sc, cudaStream_t st, int num_sms, cudaEvent_t *ev)
 {
-    static int g_march = 0, g_march2 = 0, g_bisect = 0;
+    static std::atomic<int> g_march{0}, g_march2{0}, g_bisect{0};
     const unsigned ntiles = (unsigned)fd.tiles_x * (unsigned)fd.tiles_y;
     if (ev) cudaEventRecord(ev[0], st);
     if constexpr (sizeof(T) == 4) {
         if (fd.march_variant == 1) {
-            if (!g_march2) g_march2 = persistent_grid(march2_kernel<SQ, MOD, RECHECK, false>, num_sms);
-            const int gm = (int)min((unsigned)g_march2, (ntiles + 3u) / 4u);
+            const int cap = num_sms * resident_per_sm(g_march2, march2_kernel<SQ, MOD, RECHECK, false>);
+            const int gm = (int)min((unsigned)cap, (ntiles + 3u) / 4u);
             if (fd.axis_slice)
                 march2_kernel<SQ, MOD, RECHECK, true><<<gm > 0 ? gm : 1, kBlock, 0, st>>>(fd, sc);
             else
@@ -354,23 +345,21 @@ cudaError_t launch_passes(const FrameDesc &fd, const Scratch &sc, cudaStream_t s
         }
     }
     if (sizeof(T) != 4 || fd.march_variant != 1) {
-        if (!g_march) g_march = persistent_grid(march_kernel<T, SQ, MOD, RECHECK>, num_sms);
-        const int gm = (int)min((unsigned)g_march, (ntiles + 3u) / 4u);
+        const int cap = num_sms * resident_per_sm(g_march, march_kernel<T, SQ, MOD, RECHECK>);
+        const int gm = (int)min((unsigned)cap, (ntiles + 3u) / 4u);
         march_kernel<T, SQ, MOD, RECHECK><<<gm > 0 ? gm : 1, kBlock, 0, st>>>(fd, sc);
     }
     if (ev) cudaEventRecord(ev[1], st);
-    if (!g_bisect) g_bisect = persistent_grid(bisect_kernel<T, SQ, MOD, RECHECK>, num_sms);
+    const int capb = num_sms * resident_per_sm(g_bisect, bisect_kernel<T, SQ, MOD, RECHECK>);
     const unsigned maxw = ((unsigned)fd.W * (unsigned)fd.H + 31u) / 32u;
-    const int gb = (int)min((unsigned)g_bisect, (maxw + 3u) / 4u);
+    const int gb = (int)min((unsigned)capb, (maxw + 3u) / 4u);
     bisect_kernel<T, SQ, MOD, RECHECK><<<gb > 0 ? gb : 1, kBlock, 0, st>>>(fd, sc);
     if (ev) cudaEventRecord(ev[2], st);
     if (RECHECK) {
-        static int g_re = 0, g_fx = 0;
-        if (!g_re) g_re = persistent_grid(recheck_kernel<SQ, MOD>, num_sms);
-        if (!g_fx) g_fx = persistent_grid(fixup_kernel<SQ, MOD>, num_sms);
-        recheck_kernel<SQ, MOD><<<g_re, kBlock, 0, st>>>(fd, sc);
+        static std::atomic<int> g_re{0}, g_fx{0};
+        recheck_kernel<SQ, MOD><<<num_sms * resident_per_sm(g_re, recheck_kernel<SQ, MOD>), kBlock, 0, st>>>(fd, sc);
         if (ev) cudaEventRecord(ev[3], st);
-        fixup_kernel<SQ, MOD><<<g_fx, kBlock, 0, st>>>(fd, sc);
+        fixup_kernel<SQ, MOD><<<num_sms * resident_per_sm(g_fx, fixup_kernel<SQ, MOD>), kBlock, 0, st>>>(fd, sc);
         if (ev) cudaEventRecord(ev[4], st);
     } else if (ev) {
         cudaEventRecord(ev[3], st);

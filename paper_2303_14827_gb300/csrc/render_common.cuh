@@ -4,12 +4,32 @@
 // and bisection passes.
 #pragma once
 
+#include <atomic>
+
 #include "dq_math.cuh"
 
 namespace dqj {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kBlock = 128;  // 4 warps per CTA
+
+// Resident CTAs of `kernel` per SM at kBlock threads, cached in `slot` (one slot
+// per kernel instantiation).  The count depends on the kernel's registers and
+// shared memory only, so it holds for every device of this single-architecture
+// build; callers multiply it by the launching device's SM count.  Threads that
+// race on an empty slot compute and store the same value.
+template <typename K>
+inline int resident_per_sm(std::atomic<int> &slot, K kernel)
+{
+    int v = slot.load(std::memory_order_relaxed);
+    if (v > 0) return v;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kernel, kBlock, 0) != cudaSuccess || v < 1) {
+        cudaGetLastError();
+        return 1;
+    }
+    slot.store(v, std::memory_order_relaxed);
+    return v;
+}
 
 // Per-lane counters, added to the frame's stats once per warp (DQJ_STAT_*).
 struct LaneStats {

@@ -217,13 +217,8 @@ __global__ void __launch_bounds__(kBlock, 4) serve_kernel(ServeCtl ctl)
 
 cudaError_t serve_launch(const ServeCtl &ctl, int num_sms, cudaStream_t st)
 {
-    static int per_sm = 0;
-    if (!per_sm) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, serve_kernel, kBlock, 0) != cudaSuccess ||
-            per_sm < 1)
-            per_sm = 1;
-    }
-    serve_kernel<<<per_sm * num_sms, kBlock, 0, st>>>(ctl);
+    static std::atomic<int> per_sm{0};
+    serve_kernel<<<num_sms * resident_per_sm(per_sm, serve_kernel), kBlock, 0, st>>>(ctl);
     return cudaGetLastError();
 }
 

@@ -249,24 +249,16 @@ __global__ void __launch_bounds__(kBlock) voxel_overflow_kernel(const __grid_con
     flush_stat(&va.ctr->stats[3], (unsigned long long)delta);
 }
 
-template <typename K>
-int grid_of(K kernel, int num_sms)
-{
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, 0) != cudaSuccess || per_sm < 1)
-        per_sm = 1;
-    return per_sm * num_sms;
-}
-
 template <int SQ, int MOD>
 cudaError_t launch_voxels_t(const FrameDesc &fd, const VoxelArgs &va, cudaStream_t st, int num_sms)
 {
+    static std::atomic<int> g64{0}, g2{0}, gre{0}, gov{0};
     if (fd.precision == DQJ_FP64) {
-        voxel64_kernel<SQ, MOD><<<grid_of(voxel64_kernel<SQ, MOD>, num_sms), kBlock, 0, st>>>(fd, va);
+        voxel64_kernel<SQ, MOD><<<num_sms * resident_per_sm(g64, voxel64_kernel<SQ, MOD>), kBlock, 0, st>>>(fd, va);
         return cudaGetLastError();
     }
     const bool re = fd.precision == DQJ_FP32_RECHECK;
-    const int gm = (int)min((uint64_t)grid_of(voxel2_kernel<SQ, MOD, false, false>, num_sms),
+    const int gm = (int)min((uint64_t)num_sms * resident_per_sm(g2, voxel2_kernel<SQ, MOD, false, false>),
                             (va.nsegs + 4 * kBatch - 1) / (4 * kBatch));
     const int gg = gm > 0 ? gm : 1;
     if (re) {
@@ -274,8 +266,8 @@ cudaError_t launch_voxels_t(const FrameDesc &fd, const VoxelArgs &va, cudaStream
             voxel2_kernel<SQ, MOD, true, true><<<gg, kBlock, 0, st>>>(fd, va);
         else
             voxel2_kernel<SQ, MOD, true, false><<<gg, kBlock, 0, st>>>(fd, va);
-        voxel_recheck_kernel<SQ, MOD><<<grid_of(voxel_recheck_kernel<SQ, MOD>, num_sms), kBlock, 0, st>>>(fd, va);
-        voxel_overflow_kernel<SQ, MOD><<<grid_of(voxel_overflow_kernel<SQ, MOD>, num_sms), kBlock, 0, st>>>(fd, va);
+        voxel_recheck_kernel<SQ, MOD><<<num_sms * resident_per_sm(gre, voxel_recheck_kernel<SQ, MOD>), kBlock, 0, st>>>(fd, va);
+        voxel_overflow_kernel<SQ, MOD><<<num_sms * resident_per_sm(gov, voxel_overflow_kernel<SQ, MOD>), kBlock, 0, st>>>(fd, va);
     } else if (fd.axis_slice) {
         voxel2_kernel<SQ, MOD, false, true><<<gg, kBlock, 0, st>>>(fd, va);
     } else {
