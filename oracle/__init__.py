@@ -148,6 +148,9 @@ def lib():
             L.or_voxelize.argtypes = [ctypes.POINTER(Scene), ctypes.c_int32, _I64, ctypes.c_int64, ctypes.c_int,
                                       _U8, _I32, _I64]
             L.or_voxelize.restype = ctypes.c_int
+            L.or_voxel_render.argtypes = [ctypes.POINTER(Scene), ctypes.c_int32, _U8, ctypes.c_int, _I64,
+                                          ctypes.c_int64, ctypes.c_int, _I32, _D, _D, _U8, _D]
+            L.or_voxel_render.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -371,6 +374,38 @@ def voxelize(p: dict, g: int, cells=None, threads: int = 0) -> dict:
                              ctypes.byref(it))
     return {"occupancy": occ.reshape(shape), "count": cnt.reshape(shape), "iters": int(it.value),
             "threads": int(used)}
+
+
+def voxel_render(p: dict, occupancy, pixels=None, brute: bool = False, threads: int = 0) -> dict:
+    """Image of a g^3 occupancy grid (u8, indexed [k, j, i] or flat) from the
+    scene camera (Fig. voxels): the first occupied cube each pixel's ray
+    crosses, found by the cell-by-cell walk, or with brute=True by the plain
+    definition over all cubes (tiny grids).  Returns iter (cells crossed up to
+    the hit), depth, normal (face normal), rgba, and gap, the smallest margin of
+    a floating-point decision of the walk per pixel; shapes as render()."""
+    s = make_scene(p)
+    occ = np.ascontiguousarray(np.asarray(occupancy, dtype=np.uint8).reshape(-1))
+    g = int(round(occ.size ** (1.0 / 3.0)))
+    if g ** 3 != occ.size:
+        raise ValueError("occupancy must hold g^3 cells")
+    if pixels is None:
+        n = int(p["width"]) * int(p["height"])
+        shape = (int(p["height"]), int(p["width"]))
+        pix_arr = None
+    else:
+        pix_arr = np.ascontiguousarray(np.asarray(pixels, dtype=np.int64).reshape(-1))
+        n, shape = pix_arr.size, (pix_arr.size,)
+    it = np.zeros(n, np.int32)
+    dep = np.zeros(n, np.float64)
+    nor = np.zeros((n, 3), np.float64)
+    rgba = np.zeros((n, 4), np.uint8)
+    gap = np.zeros(n, np.float64)
+    used = lib().or_voxel_render(ctypes.byref(s), g, occ.ctypes.data_as(_U8), 1 if brute else 0,
+                                 pix_arr.ctypes.data_as(_I64) if pix_arr is not None else None, ctypes.c_int64(n),
+                                 int(threads), it.ctypes.data_as(_I32), _dp(dep), _dp(nor),
+                                 rgba.ctypes.data_as(_U8), _dp(gap))
+    return {"iter": it.reshape(shape), "depth": dep.reshape(shape), "normal": nor.reshape(shape + (3,)),
+            "rgba": rgba.reshape(shape + (4,)), "gap": gap.reshape(shape), "threads": int(used)}
 
 
 def de_distance(p: dict, point) -> tuple:

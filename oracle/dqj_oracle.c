@@ -790,3 +790,285 @@ int or_voxelize(const or_scene *s, int32_t g, const int64_t *idx, int64_t n, int
     if (iters) *iters = atomic_load(&jb.iters);
     return started + 1;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Image of a voxel grid from the scene camera (Fig. voxels compares the     */
+/* ray-traced image with renders of 50^3 and 100^3 grids).  Reading: a grid   */
+/* is drawn as the union of its occupied cells, each the closed cube          */
+/* [box_min + idx s, box_min + (idx + 1) s] per axis, s = (box_max -          */
+/* box_min) / G; a pixel shows the first such cube its camera ray crosses.    */
+/*   depth  = the ray parameter where the ray enters that cube (t_in of the   */
+/*            box when the first cell crossed is occupied); +inf on a miss;   */
+/*   normal = outward unit normal of the entered face, -sign(d_a) e_a, a the  */
+/*            axis of that face (-d when the eye is inside the hit cube);     */
+/*   iter   = cells crossed up to and including the hit cube (all cells       */
+/*            crossed inside the box on a miss, 0 when the ray misses the     */
+/*            box);                                                           */
+/*   rgba   = Eq. phong with that normal, as for the ray-traced image.        */
+/* Two forms: the cell-by-cell walk along the ray (Amanatides and Woo's grid  */
+/* traversal, 1987) and, for tiny grids, the plain definition: the smallest   */
+/* entry parameter over all occupied cubes the ray crosses with positive      */
+/* length.                                                                    */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    int32_t iter;
+    int32_t axis;   /* axis of the entered face, -1 when the eye is inside the hit cube, -2 on a miss */
+    double depth;
+    double gap;     /* smallest margin of a floating-point decision of the walk (scene units) */
+} vox_hit;
+
+static void vox_shade(const or_scene *s, const double *d, int axis, double *normal, uint8_t *rgba)
+{
+    if (axis < 0) {
+        normal[0] = -d[0];
+        normal[1] = -d[1];
+        normal[2] = -d[2];
+    } else {
+        normal[0] = normal[1] = normal[2] = 0.0;
+        normal[axis] = d[axis] > 0.0 ? -1.0 : 1.0;
+    }
+    double l[3] = {s->light_dir[0], s->light_dir[1], s->light_dir[2]};
+    v3_normalize(l);
+    double ndl = v3_dot(normal, l);
+    double spec = 0.0;
+    if (s->k_specular > 0.0 && ndl > 0.0) {
+        double r[3], rv = 0.0;
+        for (int a = 0; a < 3; ++a) r[a] = 2.0 * ndl * normal[a] - l[a];
+        for (int a = 0; a < 3; ++a) rv -= r[a] * d[a];
+        if (rv > 0.0) spec = s->k_specular * pow(rv, s->shininess);
+    }
+    if (ndl < 0.0) ndl = 0.0;
+    double v = s->k_ambient + s->k_diffuse * ndl + spec;
+    if (v < 0.0) v = 0.0;
+    if (v > 1.0) v = 1.0;
+    rgba[0] = to_u8(v * s->albedo[0]);
+    rgba[1] = to_u8(v * s->albedo[1]);
+    rgba[2] = to_u8(v * s->albedo[2]);
+    rgba[3] = 255;
+}
+
+/* Axis whose slab the ray enters last at the box entry (the face it comes in
+ * through); -1 when t_in was clipped to 0 (eye inside the box). */
+static int box_entry_axis(const or_scene *s, const double *o, const double *d)
+{
+    double best = -INFINITY;
+    int axis = -1;
+    for (int a = 0; a < 3; ++a) {
+        if (d[a] == 0.0) continue;
+        double ta = (s->box_min[a] - o[a]) / d[a];
+        double tb = (s->box_max[a] - o[a]) / d[a];
+        double te = ta < tb ? ta : tb;
+        if (te > best) {
+            best = te;
+            axis = a;
+        }
+    }
+    return best < 0.0 ? -1 : axis;
+}
+
+/* The walk: start in the cell that holds the box entry point, then step to the
+ * neighbour across whichever cell face the ray reaches first. */
+static vox_hit voxel_walk(const or_scene *s, int32_t g, const uint8_t *occ, const double *o, const double *d)
+{
+    vox_hit h = {0, -2, INFINITY, INFINITY};
+    double t_in, t_out;
+    if (!or_box_clip(s, o, d, &t_in, &t_out)) return h;
+    double size[3], p[3];
+    int64_t idx[3], stp[3];
+    double tmax[3], tdel[3];
+    int entry = box_entry_axis(s, o, d);
+    ray_point(o, d, t_in, p);
+    for (int a = 0; a < 3; ++a) {
+        size[a] = (s->box_max[a] - s->box_min[a]) / (double)g;
+        double u = (p[a] - s->box_min[a]) / size[a];
+        double f = floor(u);
+        if (a != entry) {
+            /* margin of the cell choice: distance of the entry point to the
+             * nearest cell plane of this axis */
+            double m = fabs(u - floor(u + 0.5)) * size[a];
+            if (m < h.gap) h.gap = m;
+        }
+        if (f < 0.0) f = 0.0;
+        if (f > (double)(g - 1)) f = (double)(g - 1);
+        idx[a] = (int64_t)f;
+        if (d[a] > 0.0) {
+            stp[a] = 1;
+            tmax[a] = (s->box_min[a] + (double)(idx[a] + 1) * size[a] - o[a]) / d[a];
+            tdel[a] = size[a] / d[a];
+        } else if (d[a] < 0.0) {
+            stp[a] = -1;
+            tmax[a] = (s->box_min[a] + (double)idx[a] * size[a] - o[a]) / d[a];
+            tdel[a] = -size[a] / d[a];
+        } else {
+            stp[a] = 0;
+            tmax[a] = INFINITY;
+            tdel[a] = INFINITY;
+        }
+    }
+    int axis = entry;
+    double t = t_in;
+    for (int64_t n = 1;; ++n) {
+        if (occ[(idx[2] * g + idx[1]) * g + idx[0]]) {
+            h.iter = (int32_t)n;
+            h.axis = axis;
+            h.depth = t;
+            return h;
+        }
+        /* next face: the smallest tmax, ties to the lower axis */
+        int a = 0;
+        for (int b = 1; b < 3; ++b)
+            if (tmax[b] < tmax[a]) a = b;
+        for (int b = 0; b < 3; ++b)
+            if (b != a && tmax[b] - tmax[a] < h.gap) h.gap = tmax[b] - tmax[a];
+        idx[a] += stp[a];
+        if (idx[a] < 0 || idx[a] >= g) {
+            h.iter = (int32_t)n;
+            return h;
+        }
+        t = tmax[a];
+        tmax[a] += tdel[a];
+        axis = a;
+    }
+}
+
+/* The plain definition, by brute force over every occupied cube (tiny grids). */
+static vox_hit voxel_brute(const or_scene *s, int32_t g, const uint8_t *occ, const double *o, const double *d)
+{
+    vox_hit h = {0, -2, INFINITY, INFINITY};
+    double t_in, t_out;
+    if (!or_box_clip(s, o, d, &t_in, &t_out)) return h;
+    double size[3];
+    for (int a = 0; a < 3; ++a) size[a] = (s->box_max[a] - s->box_min[a]) / (double)g;
+    int32_t crossed_before = 0;
+    for (int64_t lin = 0; lin < (int64_t)g * g * g; ++lin) {
+        int64_t ix[3] = {lin % g, (lin / g) % g, lin / ((int64_t)g * g)};
+        double t0 = t_in, t1 = t_out;
+        int ax = -1;
+        for (int a = 0; a < 3; ++a) {
+            double lo = s->box_min[a] + (double)ix[a] * size[a];
+            double hi = s->box_min[a] + (double)(ix[a] + 1) * size[a];
+            if (d[a] == 0.0) {
+                if (o[a] < lo || o[a] > hi) t1 = -INFINITY;
+                continue;
+            }
+            double ta = (lo - o[a]) / d[a], tb = (hi - o[a]) / d[a];
+            if (ta > tb) {
+                double tmp = ta;
+                ta = tb;
+                tb = tmp;
+            }
+            if (ta > t0) {
+                t0 = ta;
+                ax = a;
+            }
+            if (tb < t1) t1 = tb;
+        }
+        if (!(t0 < t1) || !occ[lin]) continue;
+        if (t0 < h.depth) {
+            h.depth = t0;
+            h.axis = ax;
+        }
+    }
+    if (h.axis == -1 && t_in > 0.0) h.axis = box_entry_axis(s, o, d);
+    /* cells crossed up to the hit: those whose entry lies before the hit's */
+    for (int64_t lin = 0; lin < (int64_t)g * g * g; ++lin) {
+        int64_t ix[3] = {lin % g, (lin / g) % g, lin / ((int64_t)g * g)};
+        double t0 = t_in, t1 = t_out;
+        for (int a = 0; a < 3; ++a) {
+            double lo = s->box_min[a] + (double)ix[a] * size[a];
+            double hi = s->box_min[a] + (double)(ix[a] + 1) * size[a];
+            if (d[a] == 0.0) {
+                if (o[a] < lo || o[a] > hi) t1 = -INFINITY;
+                continue;
+            }
+            double ta = (lo - o[a]) / d[a], tb = (hi - o[a]) / d[a];
+            if (ta > tb) {
+                double tmp = ta;
+                ta = tb;
+                tb = tmp;
+            }
+            if (ta > t0) t0 = ta;
+            if (tb < t1) t1 = tb;
+        }
+        if (t0 < t1 && t0 <= h.depth) ++crossed_before;
+    }
+    h.iter = crossed_before;
+    return h;
+}
+
+typedef struct {
+    const or_scene *s;
+    int32_t g;
+    const uint8_t *occ;
+    int brute;
+    const int64_t *pix;
+    int64_t npix;
+    int32_t *iter;
+    double *depth, *normal, *gap;
+    uint8_t *rgba;
+    atomic_llong next;
+} vrender_job;
+
+static void *vrender_worker(void *arg)
+{
+    vrender_job *jb = (vrender_job *)arg;
+    for (;;) {
+        int64_t start = atomic_fetch_add(&jb->next, CHUNK);
+        if (start >= jb->npix) break;
+        int64_t end = start + CHUNK < jb->npix ? start + CHUNK : jb->npix;
+        for (int64_t q = start; q < end; ++q) {
+            int64_t lin = jb->pix ? jb->pix[q] : q;
+            int i = (int)(lin % jb->s->width), j = (int)(lin / jb->s->width);
+            double o[3], d[3], n[3] = {0.0, 0.0, 0.0};
+            uint8_t c[4] = {0, 0, 0, 0};
+            or_camera_ray(jb->s, i, j, o, d);
+            vox_hit h = jb->brute ? voxel_brute(jb->s, jb->g, jb->occ, o, d)
+                                  : voxel_walk(jb->s, jb->g, jb->occ, o, d);
+            if (h.axis != -2) vox_shade(jb->s, d, h.axis, n, c);
+            if (jb->iter) jb->iter[q] = h.iter;
+            if (jb->depth) jb->depth[q] = h.depth;
+            if (jb->normal) memcpy(jb->normal + 3 * q, n, sizeof n);
+            if (jb->rgba) memcpy(jb->rgba + 4 * q, c, sizeof c);
+            if (jb->gap) jb->gap[q] = h.gap;
+        }
+    }
+    return NULL;
+}
+
+/*
+ * Image of the g^3 occupancy grid occ (linear index (k g + j) g + i) from the
+ * scene camera, by the walk (brute = 0) or by the plain definition (brute = 1,
+ * tiny grids only).  pix / npix / outputs as or_render; gap (optional) gets, per
+ * output, the smallest margin of a floating-point decision the walk took (the
+ * cell of the entry point and each choice of the next face), in scene units.
+ * Returns the number of threads used.
+ */
+int or_voxel_render(const or_scene *s, int32_t g, const uint8_t *occ, int brute, const int64_t *pix, int64_t npix,
+                    int nthreads, int32_t *iter, double *depth, double *normal, uint8_t *rgba, double *gap)
+{
+    vrender_job jb;
+    memset(&jb, 0, sizeof jb);
+    jb.s = s;
+    jb.g = g;
+    jb.occ = occ;
+    jb.brute = brute;
+    jb.pix = pix;
+    jb.npix = pix ? npix : (int64_t)s->width * (int64_t)s->height;
+    jb.iter = iter;
+    jb.depth = depth;
+    jb.normal = normal;
+    jb.rgba = rgba;
+    jb.gap = gap;
+    atomic_init(&jb.next, 0);
+    if (nthreads <= 0) nthreads = or_default_threads();
+    if (nthreads > 1024) nthreads = 1024;
+    pthread_t th[1024];
+    int started = 0;
+    for (int t = 1; t < nthreads; ++t) {
+        if (pthread_create(&th[started], NULL, vrender_worker, &jb) != 0) break;
+        ++started;
+    }
+    vrender_worker(&jb);
+    for (int t = 0; t < started; ++t) pthread_join(th[t], NULL);
+    return started + 1;
+}
