@@ -311,6 +311,38 @@ dqj_status dqj_pass_ms(dqj_ctx *ctx, int32_t frames, float *ms);
 dqj_status dqj_voxelize(dqj_ctx *ctx, const dqj_params *p, int32_t grid_n, uint8_t *occupancy, uint16_t *counts,
                         int64_t *stats, void *cuda_stream);
 
+/*
+ * dqj_render_voxels -- image of a voxel grid from the scene camera (Fig. voxels
+ * sets the ray-traced image beside renders of 50^3 and 100^3 voxel grids; the
+ * paper drew its cubes with a geometry shader, here each camera ray walks the
+ * grid).
+ *
+ * The grid is drawn as the union of its occupied cells, cell (i, j, k) being the
+ * closed cube box_min + [idx, idx + 1] (box_max - box_min) / grid_n per axis.
+ * Each pixel's camera ray (eye, target, up, fov_y_deg, width, height: the
+ * camera of dqj_render) shows the first occupied cube it crosses, found by
+ * walking the ray through the grid cell by cell in FP64.  Outputs, as for
+ * dqj_render (caller-owned device planes, any may be NULL, pitch_px >= width,
+ * 4-byte aligned):
+ *   iter    cells the ray crossed up to and including the hit cube; on a miss
+ *           all cells it crossed (0 when it misses the box);
+ *   depth   ray parameter at which the ray enters the hit cube (the box entry
+ *           when the first cell is occupied); +inf on a miss;
+ *   normal  outward normal of the face entered, -sign(d_a) e_a (-d when the eye
+ *           is inside the hit cube); (0,0,0) on a miss;
+ *   rgba    the ambient, diffuse and (k_specular > 0) specular terms of Eq. phong
+ *           with that normal; (0,0,0,0) on a miss.
+ * occupancy is grid_n^3 bytes of device memory, nonzero = occupied, linear index
+ * (k grid_n + j) grid_n + i as written by dqj_voxelize.  The Julia, march and
+ * precision fields of p are validated but unused.  Stream-ordered on
+ * cuda_stream; uses no context memory.  A choice between two cell faces that
+ * lie within rounding of each other may go either way.  Errors: DQJ_ERR_INVALID
+ * for a bad p or outputs, grid_n outside 1..DQJ_VOXEL_MAX_GRID, NULL occupancy
+ * or a mock context; DQJ_ERR_CUDA for a failed launch.
+ */
+dqj_status dqj_render_voxels(dqj_ctx *ctx, const dqj_params *p, int32_t grid_n, const uint8_t *occupancy,
+                             const dqj_outputs *out, void *cuda_stream);
+
 /* Largest width * height dqj_render_noalloc accepts (e.g. 512 x 512). */
 #define DQJ_NOALLOC_MAX_PIXELS 262144u
 

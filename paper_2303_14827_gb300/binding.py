@@ -138,6 +138,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         L.dqj_serve_stats.argtypes = [ctypes.c_void_p, P(ctypes.c_int64)]
         L.dqj_voxelize.argtypes = [ctypes.c_void_p, P(dqj_params), ctypes.c_int32, ctypes.c_void_p,
                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        L.dqj_render_voxels.argtypes = [ctypes.c_void_p, P(dqj_params), ctypes.c_int32, ctypes.c_void_p,
+                                        P(dqj_outputs), ctypes.c_void_p]
         for name in declared_symbols():
             fn = getattr(L, name)
             if name != "dqj_last_error":
@@ -315,6 +317,14 @@ def dqj_voxelize(ctx: int, scene: dict, grid_n: int, occupancy=None, counts=None
     p = make_params(scene)
     check(load().dqj_voxelize(ctypes.c_void_p(ctx), ctypes.byref(p), int(grid_n), _ptr(occupancy), _ptr(counts),
                               _ptr(stats), ctypes.c_void_p(stream)))
+
+
+def dqj_render_voxels(ctx: int, scene: dict, grid_n: int, occupancy, outputs: dqj_outputs, stream: int = 0) -> None:
+    """Image of a grid_n^3 occupancy grid (device uint8, as dqj_voxelize writes
+    it) from the scene camera into caller-owned planes (see make_outputs)."""
+    p = make_params(scene)
+    check(load().dqj_render_voxels(ctypes.c_void_p(ctx), ctypes.byref(p), int(grid_n), _ptr(occupancy),
+                                   ctypes.byref(outputs), ctypes.c_void_p(stream)))
 
 
 SERVE_STAT_NAMES = ("launches", "restarts", "packed", "plain", "batches", "admit_ns", "completed", "loops")

@@ -400,7 +400,7 @@ static dqj_status enqueue_frame(dqj_ctx *ctx, const dqj_params &p, const dqj_out
     return DQJ_OK;
 }
 
-static dqj_status check_outputs(const dqj_params &p, const dqj_outputs *out)
+dqj_status check_outputs(const dqj_params &p, const dqj_outputs *out)
 {
     if (!out) return fail(DQJ_ERR_INVALID, "outputs is NULL");
     if (out->pitch_px < p.width) return fail(DQJ_ERR_INVALID, "pitch_px must be >= width");

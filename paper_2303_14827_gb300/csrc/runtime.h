@@ -22,6 +22,8 @@ dqj_status cuda_fail(cudaError_t e, const char *what);
 
 // Validation and derivation of the per-frame constants (host, double).
 dqj_status validate(const dqj_params *p);
+// Output planes: pitch >= width, every non-NULL plane 4-byte aligned.
+dqj_status check_outputs(const dqj_params &p, const dqj_outputs *out);
 void derive_frame(const dqj_params &p, FrameDesc &fd, int tile_w, int tile_h);
 // Exact thresholds of the axis-slice first step's tests (see PairConsts).
 void axis_first_thresholds(const FrameT<float> &F, int modulus_mode, PairConsts &P);

@@ -96,6 +96,34 @@ def test_voxelize_validation_on_a_mock_context(monkeypatch):
     assert re.search(r"#define DQJ_VOXEL_MAX_GRID (\d+)", text).group(1) == str(binding.DQJ_VOXEL_MAX_GRID)
 
 
+def test_render_voxels_validation_on_a_mock_context():
+    ctx = binding.dqj_create(-1)
+    try:
+        s = scenes.default_scene(width=64, height=48)
+        good = binding.make_outputs(pitch_px=64, depth=4096)
+        for g in (0, binding.DQJ_VOXEL_MAX_GRID + 1):
+            with pytest.raises(binding.DqjError) as ei:
+                binding.dqj_render_voxels(ctx, s, g, 4096, good)
+            assert ei.value.status == binding.DQJ_ERR_INVALID and "grid_n" in binding.last_error()
+        with pytest.raises(binding.DqjError):
+            binding.dqj_render_voxels(ctx, s, 8, None, good)
+        assert "occupancy" in binding.last_error()
+        with pytest.raises(binding.DqjError):
+            binding.dqj_render_voxels(ctx, s, 8, 4096, binding.make_outputs(pitch_px=63, depth=4096))
+        assert "pitch" in binding.last_error()
+        with pytest.raises(binding.DqjError):
+            binding.dqj_render_voxels(ctx, s, 8, 4096, binding.make_outputs(pitch_px=64, depth=4098))
+        assert "aligned" in binding.last_error()
+        with pytest.raises(binding.DqjError):
+            binding.dqj_render_voxels(ctx, dict(s, width=0), 8, 4096, good)
+        assert "width" in binding.last_error()
+        with pytest.raises(binding.DqjError):
+            binding.dqj_render_voxels(ctx, s, 8, 4096, good)
+        assert "mock" in binding.last_error()
+    finally:
+        binding.dqj_destroy(ctx)
+
+
 @pytest.mark.parametrize("field,value", [("traversal", 2), ("de_max_steps", 0), ("de_epsilon", 0.0),
                                          ("de_step_scale", 1.5), ("de_step_scale", 0.0), ("de_bound_radius", -1.0)])
 def test_de_validation_rejects(lib, field, value):
