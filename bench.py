@@ -480,9 +480,14 @@ def pct(v, q):
     return v[min(len(v) - 1, int(round(q * (len(v) - 1))))]
 
 
-def serving_section(local, n_sat=256, n_stream=600, rates=(1.0,)):
+POLICY_NAMES = {0: "fifo", 1: "shortest"}
+
+
+def serving_section(local, n_sat=256, n_stream=600, rates=(1.0,), policies=(0, 1)):
     """Served vs back-to-back frames/s on a burst of the serving mix, then Poisson
-    arrivals at the given fractions of the measured saturation rate."""
+    arrivals at the given fractions of the measured saturation rate, under each
+    serving policy (admission order; earliest estimated finish), with latency
+    percentiles overall and per request size."""
     import numpy as np
     import torch
 
@@ -508,12 +513,22 @@ def serving_section(local, n_sat=256, n_stream=600, rates=(1.0,)):
         rng = np.random.default_rng(2)
         gaps = rng.exponential(1.0, n_stream)
         reqs = stream_reqs[:n_stream]
-        for f in rates:
-            arr = np.cumsum(gaps / (f * sat)).tolist()
-            lat, span = served_run(ctx, reqs, arr, pool)
-            out["poisson"].append({"offered_fraction_of_saturation": f, "requests": len(reqs),
-                                   "p50_ms": 1e3 * pct(lat, 0.50), "p99_ms": 1e3 * pct(lat, 0.99),
-                                   "achieved_frames_per_s": len(reqs) / span})
+        sizes = [(s["width"], s["height"]) for s in reqs]
+        for policy in policies:
+            binding.dqj_serve_policy(ctx, policy)
+            for f in rates:
+                arr = np.cumsum(gaps / (f * sat)).tolist()
+                lat, span = served_run(ctx, reqs, arr, pool)
+                by_size = {}
+                for wh in sorted(set(sizes), key=lambda v: v[0] * v[1]):
+                    ls = [x for x, z in zip(lat, sizes) if z == wh]
+                    by_size["%dx%d" % wh] = {"n": len(ls), "p50_ms": round(1e3 * pct(ls, 0.50), 3),
+                                             "p99_ms": round(1e3 * pct(ls, 0.99), 3)}
+                out["poisson"].append({"policy": POLICY_NAMES[policy], "offered_fraction_of_saturation": f,
+                                       "requests": len(reqs), "p50_ms": 1e3 * pct(lat, 0.50),
+                                       "p99_ms": 1e3 * pct(lat, 0.99), "achieved_frames_per_s": len(reqs) / span,
+                                       "by_size": by_size})
+        binding.dqj_serve_policy(ctx, binding.DQJ_SERVE_FIFO)
         out["output_pool_misses"] = pool.misses
         out["scheduler"] = binding.dqj_serve_stats(ctx)
         return out

@@ -242,6 +242,24 @@ dqj_status dqj_submit(dqj_ctx *ctx, const dqj_params *p, const dqj_outputs *out,
 #define DQJ_NSERVE_STATS 8
 dqj_status dqj_serve_stats(dqj_ctx *ctx, int64_t *out);
 
+/* Order in which the persistent launch serves the admitted requests (requests
+ * are admitted in arrival order; those that run as plain frames are
+ * unaffected):
+ *   DQJ_SERVE_FIFO      admission order (the default);
+ *   DQJ_SERVE_SHORTEST  earliest estimated finish: each request's key is its
+ *                       arrival time at dqj_submit plus an estimate of its own
+ *                       march time (width x height x (march_steps + 1) samples
+ *                       at 2^-9 ns each).  Small requests overtake a large one
+ *                       that arrived less than their difference in cost
+ *                       earlier; no request is overtaken by one that arrives
+ *                       after its own estimated finish, so none starves.
+ * Applies to requests admitted after the call; results are unchanged (every
+ * request equals its dqj_render alone).  DQJ_ERR_INVALID for an unknown policy.
+ * An interface of this library (serving latency); the paper has no counterpart. */
+#define DQJ_SERVE_FIFO 0
+#define DQJ_SERVE_SHORTEST 1
+dqj_status dqj_serve_policy(dqj_ctx *ctx, int32_t policy);
+
 /* Non-blocking completion check.  *done = 1 and *result = the request's status
  * once finished; the ticket is then consumed (a second poll: DQJ_ERR_NOT_FOUND). */
 dqj_status dqj_poll(dqj_ctx *ctx, dqj_ticket ticket, int *done, dqj_status *result);

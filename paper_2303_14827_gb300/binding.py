@@ -138,6 +138,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         L.dqj_serve_stats.argtypes = [ctypes.c_void_p, P(ctypes.c_int64)]
         L.dqj_voxelize.argtypes = [ctypes.c_void_p, P(dqj_params), ctypes.c_int32, ctypes.c_void_p,
                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        L.dqj_serve_policy.argtypes = [ctypes.c_void_p, ctypes.c_int32]
         L.dqj_render_voxels.argtypes = [ctypes.c_void_p, P(dqj_params), ctypes.c_int32, ctypes.c_void_p,
                                         P(dqj_outputs), ctypes.c_void_p]
         for name in declared_symbols():
@@ -328,6 +329,14 @@ def dqj_render_voxels(ctx: int, scene: dict, grid_n: int, occupancy, outputs: dq
 
 
 SERVE_STAT_NAMES = ("launches", "restarts", "packed", "plain", "batches", "admit_ns", "completed", "loops")
+
+
+DQJ_SERVE_FIFO, DQJ_SERVE_SHORTEST = 0, 1
+
+
+def dqj_serve_policy(ctx: int, policy: int) -> None:
+    """Order of the persistent launch's requests (see dqj_serve_policy in dqj.h)."""
+    check(load().dqj_serve_policy(ctypes.c_void_p(ctx), int(policy)))
 
 
 def dqj_serve_stats(ctx: int) -> dict:

@@ -67,6 +67,7 @@ struct dqj_ctx {
     std::map<int, std::pair<int, int>> tiles;
     std::mutex tiles_mu;             // guards tiles (read by the serving thread too)
     dqj::ServeState *serve = nullptr;
+    std::atomic<int> serve_policy{DQJ_SERVE_FIFO};  // order of packed requests in the persistent launch
     // dqj_voxelize scratch: counter block + FP64 recheck queue; grow-only
     void *vox_scratch = nullptr;
     size_t vox_bytes = 0;

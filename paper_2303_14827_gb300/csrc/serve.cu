@@ -3,9 +3,10 @@
 //
 // The host admits a request by writing a control block (ReqBlock: frame
 // constants, counters, claim counters) and then publishing its index in a slot
-// (ServeSlot).  Each warp of the persistent grid repeatedly picks the oldest
-// published request that still has unclaimed work, claims one work item from it
-// with an atomic add and runs it:
+// (ServeSlot).  Each warp of the persistent grid repeatedly picks the published
+// request with the smallest priority key that still has unclaimed work (the
+// host sets the key: admission order, or arrival time plus the request's
+// estimated cost), claims one work item from it with an atomic add and runs it:
 //   MARCH phase : one 64-ray tile of the paired march (march2_tile);
 //   BISECT phase: 32 hit-list entries (bisect_chunk).
 // The warp that completes a request's last march tile switches it to the
@@ -108,17 +109,18 @@ __global__ void __launch_bounds__(kBlock, 4) serve_kernel(ServeCtl ctl)
     unsigned long long idle_since = 0;
     for (;;) {
         if (__shfl_sync(kFull, lane == 0 ? ld_vol32(ctl.exit_flag) : 0u, 0)) break;
-        // ---- the oldest published request with unclaimed work (two slots per lane)
+        // ---- the published request with the smallest key and unclaimed work (two slots per lane)
         unsigned long long best = ~0ull;
         int best_block = -1;
 #pragma unroll
         for (int h = 0; h < kMaxSlots / 32; ++h) {
             const ServeSlot *sl = &ctl.slots[lane + 32 * h];
-            const unsigned long long seq = ld_vol64(&sl->seq);
-            if (seq == 0 || seq >= best) continue;
+            if (ld_vol64(&sl->seq) == 0) continue;
+            const unsigned long long key = ld_vol64(&sl->prio);
+            if (key >= best) continue;
             const unsigned bi = ld_vol32(&sl->block);
             if (bi < (unsigned)kReqBlocks && has_work(&ctl.blocks[bi])) {
-                best = seq;
+                best = key;
                 best_block = (int)bi;
             }
         }

@@ -36,7 +36,8 @@ static_assert(sizeof(FrameDesc) % 16 == 0, "FrameDesc is copied as uint4");
 
 // One resident request: which control block, published by writing seq last.
 struct alignas(16) ServeSlot {
-    unsigned long long seq;         // admission sequence; 0 while empty
+    unsigned long long seq;         // admission sequence (the request's generation); 0 while empty
+    unsigned long long prio;        // warps serve the published request with the smallest prio first
     unsigned block;                 // index into the ReqBlock array
     unsigned pad;
 };

@@ -96,6 +96,21 @@ def test_voxelize_validation_on_a_mock_context(monkeypatch):
     assert re.search(r"#define DQJ_VOXEL_MAX_GRID (\d+)", text).group(1) == str(binding.DQJ_VOXEL_MAX_GRID)
 
 
+def test_serve_policy_argument_errors():
+    ctx = binding.dqj_create(-1)
+    try:
+        for policy in (binding.DQJ_SERVE_FIFO, binding.DQJ_SERVE_SHORTEST):
+            binding.dqj_serve_policy(ctx, policy)
+        with pytest.raises(binding.DqjError) as ei:
+            binding.dqj_serve_policy(ctx, 2)
+        assert ei.value.status == binding.DQJ_ERR_INVALID and "policy" in binding.last_error()
+    finally:
+        binding.dqj_destroy(ctx)
+    text = open(binding.HEADER).read()
+    assert re.search(r"#define DQJ_SERVE_FIFO (\d+)", text).group(1) == str(binding.DQJ_SERVE_FIFO)
+    assert re.search(r"#define DQJ_SERVE_SHORTEST (\d+)", text).group(1) == str(binding.DQJ_SERVE_SHORTEST)
+
+
 def test_render_voxels_validation_on_a_mock_context():
     ctx = binding.dqj_create(-1)
     try:

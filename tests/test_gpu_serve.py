@@ -58,12 +58,14 @@ def mixed_requests():
     return reqs
 
 
-def test_served_equals_alone():
+@pytest.mark.parametrize("policy", [binding.DQJ_SERVE_FIFO, binding.DQJ_SERVE_SHORTEST])
+def test_served_equals_alone(policy):
     import torch
     reqs = mixed_requests()
     with binding.Renderer(0) as rdr:
         ctx = binding.dqj_create(0)
         try:
+            binding.dqj_serve_policy(ctx, policy)
             outs, status = run_served(ctx, reqs)
             assert all(v == binding.DQJ_OK for v in status.values()), status
             for i, s in enumerate(reqs):
@@ -72,6 +74,39 @@ def test_served_equals_alone():
         finally:
             binding.dqj_destroy(ctx)
     torch.cuda.synchronize()
+
+
+def test_shortest_policy_lets_small_requests_overtake():
+    """DQJ_SERVE_SHORTEST: eight 128x128 requests submitted just after a
+    1920x1080 request with 2048 march steps (several ms) all finish before it;
+    the results still equal the requests rendered alone."""
+    import torch
+    big = dict(scenes.full_hd_scene(0), march_steps=2048)
+    small = [scenes.default_scene(width=128, height=128, c=[-0.2, 0.6, 0.2, 0.2, 0.1, 0.0, 0.0, 0.01 * k])
+             for k in range(8)]
+    reqs = [big] + small
+    ctx = binding.dqj_create(0)
+    try:
+        binding.dqj_serve_policy(ctx, binding.DQJ_SERVE_SHORTEST)
+        run_served(ctx, [small[0]])  # scheduler thread and persistent launch running
+        outs = [binding.alloc_outputs(s["width"], s["height"]) for s in reqs]
+        torch.cuda.synchronize()
+        tickets = [binding.dqj_submit(ctx, s, binding.outputs_of(o)) for s, o in zip(reqs, outs)]
+        order, pending, t0 = [], set(range(len(reqs))), time.time()
+        while pending:
+            for i in sorted(pending):
+                done, st = binding.dqj_poll(ctx, tickets[i])
+                if done:
+                    assert st == binding.DQJ_OK
+                    order.append(i)
+                    pending.discard(i)
+            assert time.time() - t0 < 60.0
+        assert order[-1] == 0, order
+        with binding.Renderer(0) as rdr:
+            for i, s in enumerate(reqs):
+                assert_same(outs[i], rdr.render(s), s, f"request {i}")
+    finally:
+        binding.dqj_destroy(ctx)
 
 
 def test_served_other_modes_equal_alone():
