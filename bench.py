@@ -483,7 +483,7 @@ def pct(v, q):
 POLICY_NAMES = {0: "fifo", 1: "shortest"}
 
 
-def serving_section(local, n_sat=256, n_stream=600, rates=(1.0,), policies=(0, 1)):
+def serving_section(local, n_sat=256, n_stream=600, rates=(0.8, 1.0), policies=(0, 1)):
     """Served vs back-to-back frames/s on a burst of the serving mix, then Poisson
     arrivals at the given fractions of the measured saturation rate, under each
     serving policy (admission order; earliest estimated finish), with latency
