@@ -88,7 +88,9 @@ enum {
  * against a mock device (for testing admission, budgets and timeouts without a
  * GPU); it cannot render.  The mock reads DQJ_MOCK_DELAY_US (run time of a
  * request, default 1000) and DQJ_MOCK_FAIL ("nomem": every admission fails,
- * "hang": no request ever completes) from the environment at dqj_create. */
+ * "hang": no request ever completes, "throw_start" / "throw_admit": a host
+ * allocation fails while serving starts / while a batch is admitted) from the
+ * environment when serving starts. */
 #define DQJ_DEVICE_MOCK (-1)
 
 /* Per-context configuration for dqj_create. */

@@ -98,87 +98,91 @@ extern "C" {
 
 dqj_status dqj_autotune(dqj_ctx *ctx, int32_t max_classes)
 {
-    if (!ctx) return fail(DQJ_ERR_INVALID, "ctx is NULL");
-    if (ctx->device == DQJ_DEVICE_MOCK) return fail(DQJ_ERR_INVALID, "a mock context cannot autotune");
-    cudaError_t e = cudaSetDevice(ctx->device);
-    if (e != cudaSuccess) return cuda_fail(e, "autotune: cudaSetDevice");
-    static const int sizes[4][2] = {{256, 256}, {512, 512}, {1024, 1024}, {1920, 1080}};
-    static const int iters[4] = {10, 16, 24, 32};
-    static const int shapes1[][2] = {{8, 8}, {16, 4}, {4, 16}, {32, 2}, {64, 1}};
-    const int nclass = max_classes > 0 && max_classes < 4 ? max_classes : 4;
-    void *planes = nullptr;
-    const size_t px_max = (size_t)sizes[nclass - 1][0] * sizes[nclass - 1][1];
-    e = cudaMalloc(&planes, px_max * 24);
-    if (e != cudaSuccess) return cuda_fail(e, "autotune: planes");
-    cudaStream_t st = nullptr;
-    cudaEvent_t a = nullptr, b = nullptr;
-    e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreate(&a);
-    if (e == cudaSuccess) e = cudaEventCreate(&b);
-    dqj_status result = e == cudaSuccess ? DQJ_OK : cuda_fail(e, "autotune: stream/events");
-    for (int sc = 0; sc < nclass && result == DQJ_OK; ++sc) {
-        for (int bk = 0; bk < 4 && result == DQJ_OK; ++bk) {
-            dqj_params p;
-            dqj_default_params(&p);
-            p.width = sizes[sc][0];
-            p.height = sizes[sc][1];
-            p.max_iter = iters[bk];
-            p.march_steps = 512;
-            p.bisect_steps = 10;
-            dqj_outputs out{};
-            char *pb = static_cast<char *>(planes);
-            const size_t px = (size_t)p.width * p.height;
-            out.pitch_px = p.width;
-            out.iter = reinterpret_cast<int32_t *>(pb);
-            out.depth = reinterpret_cast<float *>(pb + px * 4);
-            out.normal = reinterpret_cast<float *>(pb + px * 8);
-            out.rgba = reinterpret_cast<uint8_t *>(pb + px * 20);
-            float best = 1e30f;
-            std::pair<int, int> best_shape{8, 8};
-            for (const auto &sh : shapes1) {
-                {
-                    std::lock_guard<std::mutex> lk(ctx->tiles_mu);
-                    ctx->tiles[tile_key(1, sc, bk)] = {sh[0], sh[1]};
+    return dqj::guarded([&]() -> dqj_status {
+        if (!ctx) return fail(DQJ_ERR_INVALID, "ctx is NULL");
+        if (ctx->device == DQJ_DEVICE_MOCK) return fail(DQJ_ERR_INVALID, "a mock context cannot autotune");
+        cudaError_t e = cudaSetDevice(ctx->device);
+        if (e != cudaSuccess) return cuda_fail(e, "autotune: cudaSetDevice");
+        static const int sizes[4][2] = {{256, 256}, {512, 512}, {1024, 1024}, {1920, 1080}};
+        static const int iters[4] = {10, 16, 24, 32};
+        static const int shapes1[][2] = {{8, 8}, {16, 4}, {4, 16}, {32, 2}, {64, 1}};
+        const int nclass = max_classes > 0 && max_classes < 4 ? max_classes : 4;
+        void *planes = nullptr;
+        const size_t px_max = (size_t)sizes[nclass - 1][0] * sizes[nclass - 1][1];
+        e = cudaMalloc(&planes, px_max * 24);
+        if (e != cudaSuccess) return cuda_fail(e, "autotune: planes");
+        cudaStream_t st = nullptr;
+        cudaEvent_t a = nullptr, b = nullptr;
+        e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreate(&a);
+        if (e == cudaSuccess) e = cudaEventCreate(&b);
+        dqj_status result = e == cudaSuccess ? DQJ_OK : cuda_fail(e, "autotune: stream/events");
+        for (int sc = 0; sc < nclass && result == DQJ_OK; ++sc) {
+            for (int bk = 0; bk < 4 && result == DQJ_OK; ++bk) {
+                dqj_params p;
+                dqj_default_params(&p);
+                p.width = sizes[sc][0];
+                p.height = sizes[sc][1];
+                p.max_iter = iters[bk];
+                p.march_steps = 512;
+                p.bisect_steps = 10;
+                dqj_outputs out{};
+                char *pb = static_cast<char *>(planes);
+                const size_t px = (size_t)p.width * p.height;
+                out.pitch_px = p.width;
+                out.iter = reinterpret_cast<int32_t *>(pb);
+                out.depth = reinterpret_cast<float *>(pb + px * 4);
+                out.normal = reinterpret_cast<float *>(pb + px * 8);
+                out.rgba = reinterpret_cast<uint8_t *>(pb + px * 20);
+                float best = 1e30f;
+                std::pair<int, int> best_shape{8, 8};
+                for (const auto &sh : shapes1) {
+                    {
+                        std::lock_guard<std::mutex> lk(ctx->tiles_mu);
+                        ctx->tiles[tile_key(1, sc, bk)] = {sh[0], sh[1]};
+                    }
+                    float t = 1e30f;
+                    for (int rep = 0; rep < 3 && result == DQJ_OK; ++rep) {
+                        cudaEventRecord(a, st);
+                        result = render_on_stream(ctx, &p, &out, st);
+                        cudaEventRecord(b, st);
+                        e = cudaEventSynchronize(b);
+                        float ms = 0.f;
+                        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+                        if (e != cudaSuccess && result == DQJ_OK) result = cuda_fail(e, "autotune: timing");
+                        if (rep > 0 && ms < t) t = ms;  // first repetition warms up
+                    }
+                    if (t < best) {
+                        best = t;
+                        best_shape = {sh[0], sh[1]};
+                    }
                 }
-                float t = 1e30f;
-                for (int rep = 0; rep < 3 && result == DQJ_OK; ++rep) {
-                    cudaEventRecord(a, st);
-                    result = render_on_stream(ctx, &p, &out, st);
-                    cudaEventRecord(b, st);
-                    e = cudaEventSynchronize(b);
-                    float ms = 0.f;
-                    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
-                    if (e != cudaSuccess && result == DQJ_OK) result = cuda_fail(e, "autotune: timing");
-                    if (rep > 0 && ms < t) t = ms;  // first repetition warms up
-                }
-                if (t < best) {
-                    best = t;
-                    best_shape = {sh[0], sh[1]};
-                }
+                std::lock_guard<std::mutex> lk(ctx->tiles_mu);
+                ctx->tiles[tile_key(1, sc, bk)] = best_shape;
             }
-            std::lock_guard<std::mutex> lk(ctx->tiles_mu);
-            ctx->tiles[tile_key(1, sc, bk)] = best_shape;
         }
-    }
-    if (a) cudaEventDestroy(a);
-    if (b) cudaEventDestroy(b);
-    if (st) cudaStreamDestroy(st);
-    cudaFree(planes);
-    if (result != DQJ_OK) return result;
-    return write_tile_cache(ctx);
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+        if (st) cudaStreamDestroy(st);
+        cudaFree(planes);
+        if (result != DQJ_OK) return result;
+        return write_tile_cache(ctx);
+    });
 }
 
 dqj_status dqj_tile_shape(dqj_ctx *ctx, const dqj_params *p, int32_t *variant, int32_t *tile_w, int32_t *tile_h)
 {
-    if (!ctx || !p || !variant || !tile_w || !tile_h) return fail(DQJ_ERR_INVALID, "NULL argument");
-    dqj_status s = validate(p);
-    if (s != DQJ_OK) return s;
-    int v, tw, th;
-    pick_tile_shape(ctx, *p, v, tw, th);
-    *variant = v;
-    *tile_w = tw;
-    *tile_h = th;
-    return DQJ_OK;
+    return dqj::guarded([&]() -> dqj_status {
+        if (!ctx || !p || !variant || !tile_w || !tile_h) return fail(DQJ_ERR_INVALID, "NULL argument");
+        dqj_status s = validate(p);
+        if (s != DQJ_OK) return s;
+        int v, tw, th;
+        pick_tile_shape(ctx, *p, v, tw, th);
+        *variant = v;
+        *tile_w = tw;
+        *tile_h = th;
+        return DQJ_OK;
+    });
 }
 
 }  // extern "C"

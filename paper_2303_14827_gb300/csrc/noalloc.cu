@@ -43,61 +43,63 @@ dqj_status check_planes(const dqj_params &p, const dqj_outputs *out)
 
 extern "C" dqj_status dqj_render_noalloc(const dqj_params *p, const dqj_outputs *out, void *cuda_stream)
 {
-    dqj_status s = dqj::validate(p);
-    if (s != DQJ_OK) return s;
-    const uint64_t pixels = (uint64_t)p->width * (uint64_t)p->height;
-    if (pixels > DQJ_NOALLOC_MAX_PIXELS)
-        return dqj::fail(DQJ_ERR_INVALID, "dqj_render_noalloc: width * height exceeds DQJ_NOALLOC_MAX_PIXELS (" +
-                                              std::to_string(DQJ_NOALLOC_MAX_PIXELS) + ")");
-    if (p->precision == DQJ_FP32_RECHECK)
-        return dqj::fail(DQJ_ERR_INVALID, "dqj_render_noalloc supports DQJ_FP32 and DQJ_FP64 only");
-    s = check_planes(*p, out);
-    if (s != DQJ_OK) return s;
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return dqj::cuda_fail(e, "render_noalloc: cudaGetDevice");
-    if (dev < 0 || dev >= kMaxDevices) return dqj::fail(DQJ_ERR_INVALID, "render_noalloc: device ordinal too large");
-    void *base = nullptr;
-    int sms = 0;
-    {
-        std::lock_guard<std::mutex> lk(g_setup_mu);
-        if (!g_scratch_addr[dev]) {
-            void *addr = nullptr;
-            e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
-            if (e != cudaSuccess) return dqj::cuda_fail(e, "render_noalloc: cudaGetSymbolAddress");
-            int n = 0;
-            e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-            if (e != cudaSuccess) return dqj::cuda_fail(e, "render_noalloc: cudaDeviceGetAttribute");
-            g_num_sms[dev] = n;
-            g_scratch_addr[dev] = addr;
+    return dqj::guarded([&]() -> dqj_status {
+        dqj_status s = dqj::validate(p);
+        if (s != DQJ_OK) return s;
+        const uint64_t pixels = (uint64_t)p->width * (uint64_t)p->height;
+        if (pixels > DQJ_NOALLOC_MAX_PIXELS)
+            return dqj::fail(DQJ_ERR_INVALID, "dqj_render_noalloc: width * height exceeds DQJ_NOALLOC_MAX_PIXELS (" +
+                                                  std::to_string(DQJ_NOALLOC_MAX_PIXELS) + ")");
+        if (p->precision == DQJ_FP32_RECHECK)
+            return dqj::fail(DQJ_ERR_INVALID, "dqj_render_noalloc supports DQJ_FP32 and DQJ_FP64 only");
+        s = check_planes(*p, out);
+        if (s != DQJ_OK) return s;
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return dqj::cuda_fail(e, "render_noalloc: cudaGetDevice");
+        if (dev < 0 || dev >= kMaxDevices) return dqj::fail(DQJ_ERR_INVALID, "render_noalloc: device ordinal too large");
+        void *base = nullptr;
+        int sms = 0;
+        {
+            std::lock_guard<std::mutex> lk(g_setup_mu);
+            if (!g_scratch_addr[dev]) {
+                void *addr = nullptr;
+                e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
+                if (e != cudaSuccess) return dqj::cuda_fail(e, "render_noalloc: cudaGetSymbolAddress");
+                int n = 0;
+                e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+                if (e != cudaSuccess) return dqj::cuda_fail(e, "render_noalloc: cudaDeviceGetAttribute");
+                g_num_sms[dev] = n;
+                g_scratch_addr[dev] = addr;
+            }
+            base = g_scratch_addr[dev];
+            sms = g_num_sms[dev];
         }
-        base = g_scratch_addr[dev];
-        sms = g_num_sms[dev];
-    }
-    dqj::Scratch sc{};
-    sc.ctr = static_cast<dqj::Counters *>(base);
-    sc.hits = reinterpret_cast<int4 *>(static_cast<unsigned char *>(base) + kCounterBytes);
-    sc.hit_cap = DQJ_NOALLOC_MAX_PIXELS;
+        dqj::Scratch sc{};
+        sc.ctr = static_cast<dqj::Counters *>(base);
+        sc.hits = reinterpret_cast<int4 *>(static_cast<unsigned char *>(base) + kCounterBytes);
+        sc.hit_cap = DQJ_NOALLOC_MAX_PIXELS;
 
-    const bool fp64 = p->precision == DQJ_FP64;
-    dqj::FrameDesc fd;
-    dqj::derive_frame(*p, fd, 8, fp64 ? 4 : 8);
-    fd.march_variant = fp64 ? 0 : 1;
-    fd.pitch = out->pitch_px;
-    fd.iter = out->iter;
-    fd.depth = out->depth;
-    fd.normal = out->normal;
-    fd.rgba = out->rgba;
-    fd.epoch = 1;
+        const bool fp64 = p->precision == DQJ_FP64;
+        dqj::FrameDesc fd;
+        dqj::derive_frame(*p, fd, 8, fp64 ? 4 : 8);
+        fd.march_variant = fp64 ? 0 : 1;
+        fd.pitch = out->pitch_px;
+        fd.iter = out->iter;
+        fd.depth = out->depth;
+        fd.normal = out->normal;
+        fd.rgba = out->rgba;
+        fd.epoch = 1;
 
-    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-    e = cudaMemsetAsync(sc.ctr, 0, kCounterBytes, st);
-    if (e != cudaSuccess) return dqj::cuda_fail(e, "render_noalloc: clear counters");
-    e = dqj::launch_frame(fd, sc, st, sms);
-    if (e != cudaSuccess) return dqj::cuda_fail(e, "render_noalloc: kernel launch");
-    if (out->stats) {
-        e = cudaMemcpyAsync(out->stats, sc.ctr->stats, DQJ_NSTATS * sizeof(int64_t), cudaMemcpyDeviceToDevice, st);
-        if (e != cudaSuccess) return dqj::cuda_fail(e, "render_noalloc: stats copy");
-    }
-    return DQJ_OK;
+        cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+        e = cudaMemsetAsync(sc.ctr, 0, kCounterBytes, st);
+        if (e != cudaSuccess) return dqj::cuda_fail(e, "render_noalloc: clear counters");
+        e = dqj::launch_frame(fd, sc, st, sms);
+        if (e != cudaSuccess) return dqj::cuda_fail(e, "render_noalloc: kernel launch");
+        if (out->stats) {
+            e = cudaMemcpyAsync(out->stats, sc.ctr->stats, DQJ_NSTATS * sizeof(int64_t), cudaMemcpyDeviceToDevice, st);
+            if (e != cudaSuccess) return dqj::cuda_fail(e, "render_noalloc: stats copy");
+        }
+        return DQJ_OK;
+    });
 }

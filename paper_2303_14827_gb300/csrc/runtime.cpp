@@ -7,21 +7,57 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <system_error>
 
 namespace dqj {
 
 static thread_local std::string g_err;
 
+// The message is best effort: if the host cannot allocate it, the previous
+// one is cleared and the status still returns.
+static void set_error(const char *msg) noexcept
+{
+    try {
+        g_err = msg;
+    } catch (...) {
+        g_err.clear();
+    }
+}
+
 dqj_status fail(dqj_status st, const std::string &msg)
 {
-    g_err = msg;
+    set_error(msg.c_str());
     return st;
 }
 
 dqj_status cuda_fail(cudaError_t e, const char *what)
 {
-    g_err = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
-    return e == cudaErrorMemoryAllocation ? DQJ_ERR_NOMEM : DQJ_ERR_CUDA;
+    const dqj_status st = e == cudaErrorMemoryAllocation ? DQJ_ERR_NOMEM : DQJ_ERR_CUDA;
+    try {
+        g_err = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    } catch (...) {
+        set_error(what);
+    }
+    return st;
+}
+
+dqj_status exception_status() noexcept
+{
+    try {
+        throw;
+    } catch (const std::bad_alloc &) {
+        set_error("host allocation failed");
+        return DQJ_ERR_NOMEM;
+    } catch (const std::system_error &e) {  // e.g. a thread could not be started
+        set_error(e.what());
+        return DQJ_ERR_NOMEM;
+    } catch (const std::exception &e) {
+        set_error(e.what());
+        return DQJ_ERR_INVALID;
+    } catch (...) {
+        set_error("unknown C++ exception");
+        return DQJ_ERR_INVALID;
+    }
 }
 
 static bool finite_all(const double *v, int n)
@@ -438,178 +474,191 @@ const char *dqj_last_error(void) { return g_err.c_str(); }
 
 dqj_status dqj_default_params(dqj_params *p)
 {
-    if (!p) return fail(DQJ_ERR_INVALID, "params is NULL");
-    std::memset(p, 0, sizeof *p);
-    const double c[8] = {-0.2, 0.6, 0.2, 0.2, 0.1, 0.0, 0.0, 0.05};
-    for (int i = 0; i < 8; ++i) p->c[i] = c[i];
-    for (int a = 0; a < 3; ++a) p->slice_basis[a][a] = 1.0;
-    p->eye[2] = 3.5;
-    p->up[1] = 1.0;
-    p->fov_y_deg = 45.0;
-    p->width = 256;
-    p->height = 256;
-    p->max_iter = 12;
-    p->escape_radius = 4.0;
-    p->march_steps = 256;
-    p->bisect_steps = 8;
-    p->normal_h = 1e-4;
-    for (int a = 0; a < 3; ++a) {
-        p->box_min[a] = -2.0;
-        p->box_max[a] = 2.0;
-        p->light_dir[a] = 1.0;
-        p->albedo[a] = 1.0;
-    }
-    p->k_ambient = 0.15;
-    p->k_diffuse = 0.85;
-    p->precision = DQJ_FP32;
-    p->recheck_margin = 1e-3;
-    p->square_mode = DQJ_SQUARE_ALGEBRAIC;
-    p->modulus_mode = DQJ_MODULUS_EUCLID8;
-    p->k_specular = 0.0;
-    p->shininess = 32.0;
-    p->traversal = DQJ_TRAVERSAL_MARCH;
-    p->de_max_steps = 512;
-    p->de_epsilon = 1e-3;
-    p->de_step_scale = 1.0;
-    p->de_bound_radius = 0.0;
-    return DQJ_OK;
+    return dqj::guarded([&]() -> dqj_status {
+        if (!p) return fail(DQJ_ERR_INVALID, "params is NULL");
+        std::memset(p, 0, sizeof *p);
+        const double c[8] = {-0.2, 0.6, 0.2, 0.2, 0.1, 0.0, 0.0, 0.05};
+        for (int i = 0; i < 8; ++i) p->c[i] = c[i];
+        for (int a = 0; a < 3; ++a) p->slice_basis[a][a] = 1.0;
+        p->eye[2] = 3.5;
+        p->up[1] = 1.0;
+        p->fov_y_deg = 45.0;
+        p->width = 256;
+        p->height = 256;
+        p->max_iter = 12;
+        p->escape_radius = 4.0;
+        p->march_steps = 256;
+        p->bisect_steps = 8;
+        p->normal_h = 1e-4;
+        for (int a = 0; a < 3; ++a) {
+            p->box_min[a] = -2.0;
+            p->box_max[a] = 2.0;
+            p->light_dir[a] = 1.0;
+            p->albedo[a] = 1.0;
+        }
+        p->k_ambient = 0.15;
+        p->k_diffuse = 0.85;
+        p->precision = DQJ_FP32;
+        p->recheck_margin = 1e-3;
+        p->square_mode = DQJ_SQUARE_ALGEBRAIC;
+        p->modulus_mode = DQJ_MODULUS_EUCLID8;
+        p->k_specular = 0.0;
+        p->shininess = 32.0;
+        p->traversal = DQJ_TRAVERSAL_MARCH;
+        p->de_max_steps = 512;
+        p->de_epsilon = 1e-3;
+        p->de_step_scale = 1.0;
+        p->de_bound_radius = 0.0;
+        return DQJ_OK;
+    });
 }
 
-dqj_status dqj_validate_params(const dqj_params *p) { return validate(p); }
+dqj_status dqj_validate_params(const dqj_params *p)
+{
+    return dqj::guarded([&]() -> dqj_status { return validate(p); });
+}
 
 dqj_status dqj_create(const dqj_config *cfg, dqj_ctx **out)
 {
-    if (!out) return fail(DQJ_ERR_INVALID, "out is NULL");
-    *out = nullptr;
-    dqj_config c{};
-    if (cfg) c = *cfg;
-    if (c.mem_budget_bytes == 0) c.mem_budget_bytes = 16ull << 30;
-    if (c.max_pending <= 0) c.max_pending = 4096;
-    if (c.device == DQJ_DEVICE_MOCK) {
+    return dqj::guarded([&]() -> dqj_status {
+        if (!out) return fail(DQJ_ERR_INVALID, "out is NULL");
+        *out = nullptr;
+        dqj_config c{};
+        if (cfg) c = *cfg;
+        if (c.mem_budget_bytes == 0) c.mem_budget_bytes = 16ull << 30;
+        if (c.max_pending <= 0) c.max_pending = 4096;
+        if (c.device == DQJ_DEVICE_MOCK) {
+            dqj_ctx *ctx = new (std::nothrow) dqj_ctx();
+            if (!ctx) return fail(DQJ_ERR_NOMEM, "create: out of host memory");
+            ctx->device = DQJ_DEVICE_MOCK;
+            ctx->cfg = c;
+            ctx->cfg.autotune_cache = nullptr;
+            *out = ctx;
+            return DQJ_OK;
+        }
+        int ndev = 0;
+        cudaError_t e = cudaGetDeviceCount(&ndev);
+        if (e != cudaSuccess) return cuda_fail(e, "create: cudaGetDeviceCount");
+        if (c.device < 0 || c.device >= ndev) return fail(DQJ_ERR_INVALID, "device ordinal out of range");
+        e = cudaSetDevice(c.device);
+        if (e != cudaSuccess) return cuda_fail(e, "create: cudaSetDevice");
         dqj_ctx *ctx = new (std::nothrow) dqj_ctx();
         if (!ctx) return fail(DQJ_ERR_NOMEM, "create: out of host memory");
-        ctx->device = DQJ_DEVICE_MOCK;
+        ctx->device = c.device;
         ctx->cfg = c;
+        if (c.autotune_cache) ctx->cache_path = c.autotune_cache;
         ctx->cfg.autotune_cache = nullptr;
+        e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, c.device);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->done_ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->host_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            dqj_status s = cuda_fail(e, "create");
+            if (ctx->done_ev) cudaEventDestroy(ctx->done_ev);
+            delete ctx;
+            return s;
+        }
+        load_tile_cache(ctx);
         *out = ctx;
         return DQJ_OK;
-    }
-    int ndev = 0;
-    cudaError_t e = cudaGetDeviceCount(&ndev);
-    if (e != cudaSuccess) return cuda_fail(e, "create: cudaGetDeviceCount");
-    if (c.device < 0 || c.device >= ndev) return fail(DQJ_ERR_INVALID, "device ordinal out of range");
-    e = cudaSetDevice(c.device);
-    if (e != cudaSuccess) return cuda_fail(e, "create: cudaSetDevice");
-    dqj_ctx *ctx = new (std::nothrow) dqj_ctx();
-    if (!ctx) return fail(DQJ_ERR_NOMEM, "create: out of host memory");
-    ctx->device = c.device;
-    ctx->cfg = c;
-    if (c.autotune_cache) ctx->cache_path = c.autotune_cache;
-    ctx->cfg.autotune_cache = nullptr;
-    e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, c.device);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->done_ev, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->host_stream, cudaStreamNonBlocking);
-    if (e != cudaSuccess) {
-        dqj_status s = cuda_fail(e, "create");
-        if (ctx->done_ev) cudaEventDestroy(ctx->done_ev);
-        delete ctx;
-        return s;
-    }
-    load_tile_cache(ctx);
-    *out = ctx;
-    return DQJ_OK;
+    });
 }
 
 dqj_status dqj_render(dqj_ctx *ctx, const dqj_params *p, const dqj_outputs *out, void *cuda_stream)
 {
-    if (!ctx) return fail(DQJ_ERR_INVALID, "ctx is NULL");
-    return render_on_stream(ctx, p, out, static_cast<cudaStream_t>(cuda_stream));
+    return dqj::guarded([&]() -> dqj_status {
+        if (!ctx) return fail(DQJ_ERR_INVALID, "ctx is NULL");
+        return render_on_stream(ctx, p, out, static_cast<cudaStream_t>(cuda_stream));
+    });
 }
 
 dqj_status dqj_render_host_batch(dqj_ctx *ctx, const dqj_params *p, const dqj_outputs *host_out, int32_t n)
 {
-    if (!ctx) return fail(DQJ_ERR_INVALID, "ctx is NULL");
-    if (ctx->device == DQJ_DEVICE_MOCK) return fail(DQJ_ERR_INVALID, "a mock context cannot render");
-    if (n < 0 || (n > 0 && (!p || !host_out))) return fail(DQJ_ERR_INVALID, "bad frame count or NULL arrays");
-    size_t need = 0;
-    for (int32_t i = 0; i < n; ++i) {
-        dqj_status s = validate(&p[i]);
-        if (s != DQJ_OK) return s;
-        s = check_outputs(p[i], &host_out[i]);
-        if (s != DQJ_OK) return s;
-        const size_t px = (size_t)p[i].width * (size_t)p[i].height;
-        need = std::max(need, align_up(px * 24, 256) + DQJ_NSTATS * sizeof(int64_t));
-    }
-    if (n == 0) return DQJ_OK;
-    std::lock_guard<std::mutex> lk(ctx->mu);
-    cudaError_t e = cudaSetDevice(ctx->device);
-    if (e != cudaSuccess) return cuda_fail(e, "render_host: cudaSetDevice");
-    if (!ctx->host_copy_stream) e = cudaStreamCreateWithFlags(&ctx->host_copy_stream, cudaStreamNonBlocking);
-    for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
-        if (!ctx->host_rendered[b]) e = cudaEventCreateWithFlags(&ctx->host_rendered[b], cudaEventDisableTiming);
-        if (e == cudaSuccess && !ctx->host_copied[b])
-            e = cudaEventCreateWithFlags(&ctx->host_copied[b], cudaEventDisableTiming);
-    }
-    if (e != cudaSuccess) return cuda_fail(e, "render_host: streams and events");
-    const int nbuf = n > 1 ? 2 : 1;
-    for (int b = 0; b < nbuf; ++b) {
-        if (need <= ctx->host_planes_bytes[b]) continue;
-        e = cudaStreamSynchronize(ctx->host_copy_stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->host_stream);
-        if (e == cudaSuccess && ctx->host_planes[b]) e = cudaFree(ctx->host_planes[b]);
-        ctx->host_planes[b] = nullptr;
-        ctx->host_planes_bytes[b] = 0;
-        if (e == cudaSuccess) e = cudaMalloc(&ctx->host_planes[b], need);
-        if (e != cudaSuccess) return cuda_fail(e, "render_host: device planes");
-        ctx->host_planes_bytes[b] = need;
-    }
-    cudaStream_t rs = ctx->host_stream, cs = ctx->host_copy_stream;
-    for (int32_t i = 0; i < n && e == cudaSuccess; ++i) {
-        const int b = i % nbuf;
-        const dqj_params &pi = p[i];
-        const dqj_outputs &ho = host_out[i];
-        const size_t px = (size_t)pi.width * (size_t)pi.height;
-        char *base = static_cast<char *>(ctx->host_planes[b]);
-        dqj_outputs dev{};
-        dev.pitch_px = pi.width;
-        dev.iter = ho.iter ? reinterpret_cast<int32_t *>(base) : nullptr;
-        dev.depth = ho.depth ? reinterpret_cast<float *>(base + px * 4) : nullptr;
-        dev.normal = ho.normal ? reinterpret_cast<float *>(base + px * 8) : nullptr;
-        dev.rgba = ho.rgba ? reinterpret_cast<uint8_t *>(base + px * 20) : nullptr;
-        dev.stats = ho.stats ? reinterpret_cast<int64_t *>(base + align_up(px * 24, 256)) : nullptr;
-        // the render into plane set b waits for that set's previous copy back
-        e = cudaStreamWaitEvent(rs, ctx->host_copied[b], 0);
-        if (e != cudaSuccess) break;
-        dqj_status s = enqueue_frame(ctx, pi, dev, rs);
-        if (s != DQJ_OK) {
-            cudaStreamSynchronize(cs);
-            return s;
+    return dqj::guarded([&]() -> dqj_status {
+        if (!ctx) return fail(DQJ_ERR_INVALID, "ctx is NULL");
+        if (ctx->device == DQJ_DEVICE_MOCK) return fail(DQJ_ERR_INVALID, "a mock context cannot render");
+        if (n < 0 || (n > 0 && (!p || !host_out))) return fail(DQJ_ERR_INVALID, "bad frame count or NULL arrays");
+        size_t need = 0;
+        for (int32_t i = 0; i < n; ++i) {
+            dqj_status s = validate(&p[i]);
+            if (s != DQJ_OK) return s;
+            s = check_outputs(p[i], &host_out[i]);
+            if (s != DQJ_OK) return s;
+            const size_t px = (size_t)p[i].width * (size_t)p[i].height;
+            need = std::max(need, align_up(px * 24, 256) + DQJ_NSTATS * sizeof(int64_t));
         }
-        e = cudaEventRecord(ctx->host_rendered[b], rs);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ctx->host_rendered[b], 0);
-        const size_t w = (size_t)pi.width, hp = (size_t)ho.pitch_px;
-        auto copy2d = [&](void *dst, const void *src, size_t elem) {
-            return cudaMemcpy2DAsync(dst, hp * elem, src, w * elem, w * elem, (size_t)pi.height,
-                                     cudaMemcpyDeviceToHost, cs);
-        };
-        if (e == cudaSuccess && ho.iter) e = copy2d(ho.iter, dev.iter, 4);
-        if (e == cudaSuccess && ho.depth) e = copy2d(ho.depth, dev.depth, 4);
-        if (e == cudaSuccess && ho.normal) e = copy2d(ho.normal, dev.normal, 12);
-        if (e == cudaSuccess && ho.rgba) e = copy2d(ho.rgba, dev.rgba, 4);
-        if (e == cudaSuccess && ho.stats)
-            e = cudaMemcpyAsync(ho.stats, dev.stats, DQJ_NSTATS * sizeof(int64_t), cudaMemcpyDeviceToHost, cs);
-        if (e == cudaSuccess) e = cudaEventRecord(ctx->host_copied[b], cs);
-    }
-    const cudaError_t e2 = cudaStreamSynchronize(cs);
-    if (e == cudaSuccess) e = e2;
-    if (e != cudaSuccess) return cuda_fail(e, "render_host: copy back");
-    return DQJ_OK;
+        if (n == 0) return DQJ_OK;
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        cudaError_t e = cudaSetDevice(ctx->device);
+        if (e != cudaSuccess) return cuda_fail(e, "render_host: cudaSetDevice");
+        if (!ctx->host_copy_stream) e = cudaStreamCreateWithFlags(&ctx->host_copy_stream, cudaStreamNonBlocking);
+        for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+            if (!ctx->host_rendered[b]) e = cudaEventCreateWithFlags(&ctx->host_rendered[b], cudaEventDisableTiming);
+            if (e == cudaSuccess && !ctx->host_copied[b])
+                e = cudaEventCreateWithFlags(&ctx->host_copied[b], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "render_host: streams and events");
+        const int nbuf = n > 1 ? 2 : 1;
+        for (int b = 0; b < nbuf; ++b) {
+            if (need <= ctx->host_planes_bytes[b]) continue;
+            e = cudaStreamSynchronize(ctx->host_copy_stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->host_stream);
+            if (e == cudaSuccess && ctx->host_planes[b]) e = cudaFree(ctx->host_planes[b]);
+            ctx->host_planes[b] = nullptr;
+            ctx->host_planes_bytes[b] = 0;
+            if (e == cudaSuccess) e = cudaMalloc(&ctx->host_planes[b], need);
+            if (e != cudaSuccess) return cuda_fail(e, "render_host: device planes");
+            ctx->host_planes_bytes[b] = need;
+        }
+        cudaStream_t rs = ctx->host_stream, cs = ctx->host_copy_stream;
+        for (int32_t i = 0; i < n && e == cudaSuccess; ++i) {
+            const int b = i % nbuf;
+            const dqj_params &pi = p[i];
+            const dqj_outputs &ho = host_out[i];
+            const size_t px = (size_t)pi.width * (size_t)pi.height;
+            char *base = static_cast<char *>(ctx->host_planes[b]);
+            dqj_outputs dev{};
+            dev.pitch_px = pi.width;
+            dev.iter = ho.iter ? reinterpret_cast<int32_t *>(base) : nullptr;
+            dev.depth = ho.depth ? reinterpret_cast<float *>(base + px * 4) : nullptr;
+            dev.normal = ho.normal ? reinterpret_cast<float *>(base + px * 8) : nullptr;
+            dev.rgba = ho.rgba ? reinterpret_cast<uint8_t *>(base + px * 20) : nullptr;
+            dev.stats = ho.stats ? reinterpret_cast<int64_t *>(base + align_up(px * 24, 256)) : nullptr;
+            // the render into plane set b waits for that set's previous copy back
+            e = cudaStreamWaitEvent(rs, ctx->host_copied[b], 0);
+            if (e != cudaSuccess) break;
+            dqj_status s = enqueue_frame(ctx, pi, dev, rs);
+            if (s != DQJ_OK) {
+                cudaStreamSynchronize(cs);
+                return s;
+            }
+            e = cudaEventRecord(ctx->host_rendered[b], rs);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ctx->host_rendered[b], 0);
+            const size_t w = (size_t)pi.width, hp = (size_t)ho.pitch_px;
+            auto copy2d = [&](void *dst, const void *src, size_t elem) {
+                return cudaMemcpy2DAsync(dst, hp * elem, src, w * elem, w * elem, (size_t)pi.height,
+                                         cudaMemcpyDeviceToHost, cs);
+            };
+            if (e == cudaSuccess && ho.iter) e = copy2d(ho.iter, dev.iter, 4);
+            if (e == cudaSuccess && ho.depth) e = copy2d(ho.depth, dev.depth, 4);
+            if (e == cudaSuccess && ho.normal) e = copy2d(ho.normal, dev.normal, 12);
+            if (e == cudaSuccess && ho.rgba) e = copy2d(ho.rgba, dev.rgba, 4);
+            if (e == cudaSuccess && ho.stats)
+                e = cudaMemcpyAsync(ho.stats, dev.stats, DQJ_NSTATS * sizeof(int64_t), cudaMemcpyDeviceToHost, cs);
+            if (e == cudaSuccess) e = cudaEventRecord(ctx->host_copied[b], cs);
+        }
+        const cudaError_t e2 = cudaStreamSynchronize(cs);
+        if (e == cudaSuccess) e = e2;
+        if (e != cudaSuccess) return cuda_fail(e, "render_host: copy back");
+        return DQJ_OK;
+    });
 }
 
 dqj_status dqj_render_host(dqj_ctx *ctx, const dqj_params *p, const dqj_outputs *host_out)
 {
-    if (!p || !host_out) return fail(DQJ_ERR_INVALID, "params or outputs is NULL");
-    return dqj_render_host_batch(ctx, p, host_out, 1);
+    return dqj::guarded([&]() -> dqj_status {
+        if (!p || !host_out) return fail(DQJ_ERR_INVALID, "params or outputs is NULL");
+        return dqj_render_host_batch(ctx, p, host_out, 1);
+    });
 }
 
 static void free_ring(dqj_ctx *ctx)
@@ -623,65 +672,71 @@ static void free_ring(dqj_ctx *ctx)
 
 dqj_status dqj_set_profiling(dqj_ctx *ctx, int32_t ring_frames)
 {
-    if (!ctx) return fail(DQJ_ERR_INVALID, "ctx is NULL");
-    if (ring_frames < 0 || ring_frames > 4096) return fail(DQJ_ERR_INVALID, "ring_frames must be in 0..4096");
-    std::lock_guard<std::mutex> lk(ctx->mu);
-    cudaError_t e = cudaSetDevice(ctx->device);
-    if (e == cudaSuccess && ctx->done_ev) e = cudaEventSynchronize(ctx->done_ev);
-    if (e != cudaSuccess) return cuda_fail(e, "set_profiling");
-    free_ring(ctx);
-    if (ring_frames == 0) return DQJ_OK;
-    ctx->ev.assign((size_t)ring_frames * 5, nullptr);
-    for (auto &v : ctx->ev) {
-        e = cudaEventCreate(&v);
-        if (e != cudaSuccess) {
-            free_ring(ctx);
-            return cuda_fail(e, "set_profiling: cudaEventCreate");
+    return dqj::guarded([&]() -> dqj_status {
+        if (!ctx) return fail(DQJ_ERR_INVALID, "ctx is NULL");
+        if (ring_frames < 0 || ring_frames > 4096) return fail(DQJ_ERR_INVALID, "ring_frames must be in 0..4096");
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        cudaError_t e = cudaSetDevice(ctx->device);
+        if (e == cudaSuccess && ctx->done_ev) e = cudaEventSynchronize(ctx->done_ev);
+        if (e != cudaSuccess) return cuda_fail(e, "set_profiling");
+        free_ring(ctx);
+        if (ring_frames == 0) return DQJ_OK;
+        ctx->ev.assign((size_t)ring_frames * 5, nullptr);
+        for (auto &v : ctx->ev) {
+            e = cudaEventCreate(&v);
+            if (e != cudaSuccess) {
+                free_ring(ctx);
+                return cuda_fail(e, "set_profiling: cudaEventCreate");
+            }
         }
-    }
-    ctx->ring_frames = ring_frames;
-    return DQJ_OK;
+        ctx->ring_frames = ring_frames;
+        return DQJ_OK;
+    });
 }
 
 dqj_status dqj_pass_ms(dqj_ctx *ctx, int32_t frames, float *ms)
 {
-    if (!ctx || !ms) return fail(DQJ_ERR_INVALID, "ctx or ms is NULL");
-    std::lock_guard<std::mutex> lk(ctx->mu);
-    if (frames < 1 || frames > ctx->ring_frames) return fail(DQJ_ERR_INVALID, "frames must be in 1..ring_frames");
-    if ((uint64_t)frames > ctx->ring_next) return fail(DQJ_ERR_NOT_FOUND, "fewer renders were recorded");
-    cudaError_t e = cudaSetDevice(ctx->device);
-    for (int f = 0; f < frames && e == cudaSuccess; ++f) {
-        const uint64_t idx = ctx->ring_next - (uint64_t)frames + (uint64_t)f;
-        cudaEvent_t *ev = &ctx->ev[5 * (idx % (uint64_t)ctx->ring_frames)];
-        e = cudaEventSynchronize(ev[4]);
-        for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventElapsedTime(&ms[4 * f + i], ev[i], ev[i + 1]);
-    }
-    if (e != cudaSuccess) return cuda_fail(e, "pass_ms");
-    return DQJ_OK;
+    return dqj::guarded([&]() -> dqj_status {
+        if (!ctx || !ms) return fail(DQJ_ERR_INVALID, "ctx or ms is NULL");
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        if (frames < 1 || frames > ctx->ring_frames) return fail(DQJ_ERR_INVALID, "frames must be in 1..ring_frames");
+        if ((uint64_t)frames > ctx->ring_next) return fail(DQJ_ERR_NOT_FOUND, "fewer renders were recorded");
+        cudaError_t e = cudaSetDevice(ctx->device);
+        for (int f = 0; f < frames && e == cudaSuccess; ++f) {
+            const uint64_t idx = ctx->ring_next - (uint64_t)frames + (uint64_t)f;
+            cudaEvent_t *ev = &ctx->ev[5 * (idx % (uint64_t)ctx->ring_frames)];
+            e = cudaEventSynchronize(ev[4]);
+            for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventElapsedTime(&ms[4 * f + i], ev[i], ev[i + 1]);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "pass_ms");
+        return DQJ_OK;
+    });
 }
 
 dqj_status dqj_fma_peak(int32_t device, int32_t variant, int32_t launches, double *flops_per_s)
 {
-    if (!flops_per_s) return fail(DQJ_ERR_INVALID, "flops_per_s is NULL");
-    if (variant < 0 || variant > 4) return fail(DQJ_ERR_INVALID, "variant must be in 0..4");
-    cudaError_t e = cudaSetDevice(device);
-    if (e != cudaSuccess) return cuda_fail(e, "fma_peak: cudaSetDevice");
-    int sms = 0;
-    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-    if (e != cudaSuccess) return cuda_fail(e, "fma_peak: attribute");
-    float *sink = nullptr;
-    e = cudaMalloc(&sink, (size_t)sms * 2048 * sizeof(float));
-    if (e != cudaSuccess) return cuda_fail(e, "fma_peak: cudaMalloc");
-    double best = 0.0;
-    for (int i = 0; i < (launches > 0 ? launches : 1) && e == cudaSuccess; ++i) {
-        double f = 0.0;
-        e = fma_peak_launch(variant, sms, sink, nullptr, &f);
-        if (f > best) best = f;
-    }
-    cudaFree(sink);
-    if (e != cudaSuccess) return cuda_fail(e, "fma_peak: launch");
-    *flops_per_s = best;
-    return DQJ_OK;
+    return dqj::guarded([&]() -> dqj_status {
+        if (!flops_per_s) return fail(DQJ_ERR_INVALID, "flops_per_s is NULL");
+        if (variant < 0 || variant > 4) return fail(DQJ_ERR_INVALID, "variant must be in 0..4");
+        cudaError_t e = cudaSetDevice(device);
+        if (e != cudaSuccess) return cuda_fail(e, "fma_peak: cudaSetDevice");
+        int sms = 0;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+        if (e != cudaSuccess) return cuda_fail(e, "fma_peak: attribute");
+        float *sink = nullptr;
+        e = cudaMalloc(&sink, (size_t)sms * 2048 * sizeof(float));
+        if (e != cudaSuccess) return cuda_fail(e, "fma_peak: cudaMalloc");
+        double best = 0.0;
+        for (int i = 0; i < (launches > 0 ? launches : 1) && e == cudaSuccess; ++i) {
+            double f = 0.0;
+            e = fma_peak_launch(variant, sms, sink, nullptr, &f);
+            if (f > best) best = f;
+        }
+        cudaFree(sink);
+        if (e != cudaSuccess) return cuda_fail(e, "fma_peak: launch");
+        *flops_per_s = best;
+        return DQJ_OK;
+    });
 }
 
 }  // extern "C"

@@ -19,6 +19,20 @@ namespace dqj {
 // Thread-local error message behind dqj_last_error().
 dqj_status fail(dqj_status st, const std::string &msg);
 dqj_status cuda_fail(cudaError_t e, const char *what);
+// Status for the exception in flight (call only inside a catch block): a host
+// allocation failure or a thread that could not start gives DQJ_ERR_NOMEM,
+// anything else DQJ_ERR_INVALID, each with its message.
+dqj_status exception_status() noexcept;
+// Runs an entry point's body so that no C++ exception crosses the C ABI.
+template <typename F>
+dqj_status guarded(F &&body) noexcept
+{
+    try {
+        return body();
+    } catch (...) {
+        return exception_status();
+    }
+}
 
 // Validation and derivation of the per-frame constants (host, double).
 dqj_status validate(const dqj_params *p);

@@ -21,6 +21,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <memory>
+#include <new>
 #include <vector>
 
 #include "runtime.h"
@@ -447,9 +448,12 @@ class MockBackend : public Backend {
         const char *f = std::getenv("DQJ_MOCK_FAIL");
         nomem_ = f && std::strcmp(f, "nomem") == 0;
         hang_ = f && std::strcmp(f, "hang") == 0;
+        throw_admit_ = f && std::strcmp(f, "throw_admit") == 0;
+        if (f && std::strcmp(f, "throw_start") == 0) throw std::bad_alloc();  // a host allocation that fails
     }
     void admit(Request *const *rs, int n, dqj_status *st) override
     {
+        if (throw_admit_) throw std::bad_alloc();
         for (int i = 0; i < n; ++i) {
             if (nomem_) {
                 st[i] = fail(DQJ_ERR_NOMEM, "serve (mock): injected allocation failure");
@@ -479,7 +483,7 @@ class MockBackend : public Backend {
 
   private:
     int64_t delay_us_;
-    bool nomem_ = false, hang_ = false;
+    bool nomem_ = false, hang_ = false, throw_admit_ = false;
     int running_ = 0;
 };
 
@@ -514,6 +518,7 @@ struct ServeState {
     dqj_ticket next_ticket = 1;
     uint64_t next_seq = 1;
     bool draining = false, stop = false;
+    std::atomic<bool> failed{false};  // the scheduler thread stopped on a host exception
     const clk::time_point t0 = clk::now();
     std::thread thr;
     int64_t n_packed = 0, n_plain = 0, n_batches = 0, admit_ns = 0, n_completed = 0, n_loops = 0;
@@ -525,6 +530,22 @@ struct ServeState {
         used -= r->footprint;
         finished[r->ticket] = st;
         ++n_completed;
+    }
+
+    // The scheduler thread threw (a host allocation inside it failed): queued
+    // requests end with DQJ_ERR_NOMEM and later submits are refused.  Admitted
+    // requests stay unfinished, since their device work may still be running,
+    // so dqj_destroy waits for them and reports DQJ_ERR_TIMEOUT.
+    void on_failure() noexcept
+    {
+        failed = true;
+        try {
+            std::lock_guard<std::mutex> lk(mu);
+            for (auto &r : pending) finished[r->ticket] = DQJ_ERR_NOMEM;
+            pending.clear();
+            cv.notify_all();
+        } catch (...) {
+        }
     }
 
     void loop()
@@ -618,7 +639,13 @@ dqj_status serve_start(dqj_ctx *ctx)
         st->backend = std::move(g);
     }
     ServeState *raw = st.release();
-    raw->thr = std::thread([raw] { raw->loop(); });
+    raw->thr = std::thread([raw] {
+        try {
+            raw->loop();
+        } catch (...) {
+            raw->on_failure();
+        }
+    });
     ctx->serve = raw;
     return DQJ_OK;
 }
@@ -631,145 +658,156 @@ extern "C" {
 
 dqj_status dqj_submit(dqj_ctx *ctx, const dqj_params *p, const dqj_outputs *out, dqj_ticket *ticket)
 {
-    if (!ctx || !ticket) return fail(DQJ_ERR_INVALID, "ctx or ticket is NULL");
-    dqj_status s = validate(p);
-    if (s != DQJ_OK) return s;
-    if (!out) return fail(DQJ_ERR_INVALID, "outputs is NULL");
-    if (out->pitch_px < p->width) return fail(DQJ_ERR_INVALID, "pitch_px must be >= width");
-    const void *planes[4] = {out->iter, out->depth, out->normal, out->rgba};
-    for (const void *q : planes)
-        if (q && (reinterpret_cast<uintptr_t>(q) & 3u)) return fail(DQJ_ERR_INVALID, "planes must be 4-byte aligned");
-    {
-        std::lock_guard<std::mutex> lk(ctx->mu);
-        s = serve_start(ctx);
+    return dqj::guarded([&]() -> dqj_status {
+        if (!ctx || !ticket) return fail(DQJ_ERR_INVALID, "ctx or ticket is NULL");
+        dqj_status s = validate(p);
         if (s != DQJ_OK) return s;
-    }
-    ServeState &S = *ctx->serve;
-    auto r = std::make_unique<Request>();
-    r->p = *p;
-    r->out = *out;
-    r->packed = ctx->device != DQJ_DEVICE_MOCK && packable(*p);
-    r->footprint = footprint(*p, r->packed);
-    if (r->footprint > ctx->cfg.mem_budget_bytes)
-        return fail(DQJ_ERR_NOMEM, "request footprint exceeds the context's memory budget");
-    std::lock_guard<std::mutex> lk(S.mu);
-    if (S.draining) return fail(DQJ_ERR_CANCELLED, "context is being destroyed");
-    if ((int64_t)S.pending.size() >= ctx->cfg.max_pending) return fail(DQJ_ERR_BUSY, "serving queue is full");
-    r->ticket = S.next_ticket++;
-    *ticket = r->ticket;
-    r->submitted = clk::now();
-    S.pending.push_back(std::move(r));
-    S.cv.notify_all();
-    return DQJ_OK;
+        if (!out) return fail(DQJ_ERR_INVALID, "outputs is NULL");
+        if (out->pitch_px < p->width) return fail(DQJ_ERR_INVALID, "pitch_px must be >= width");
+        const void *planes[4] = {out->iter, out->depth, out->normal, out->rgba};
+        for (const void *q : planes)
+            if (q && (reinterpret_cast<uintptr_t>(q) & 3u)) return fail(DQJ_ERR_INVALID, "planes must be 4-byte aligned");
+        {
+            std::lock_guard<std::mutex> lk(ctx->mu);
+            s = serve_start(ctx);
+            if (s != DQJ_OK) return s;
+        }
+        ServeState &S = *ctx->serve;
+        auto r = std::make_unique<Request>();
+        r->p = *p;
+        r->out = *out;
+        r->packed = ctx->device != DQJ_DEVICE_MOCK && packable(*p);
+        r->footprint = footprint(*p, r->packed);
+        if (r->footprint > ctx->cfg.mem_budget_bytes)
+            return fail(DQJ_ERR_NOMEM, "request footprint exceeds the context's memory budget");
+        std::lock_guard<std::mutex> lk(S.mu);
+        if (S.draining) return fail(DQJ_ERR_CANCELLED, "context is being destroyed");
+        if (S.failed) return fail(DQJ_ERR_NOMEM, "serving stopped after a host allocation failure");
+        if ((int64_t)S.pending.size() >= ctx->cfg.max_pending) return fail(DQJ_ERR_BUSY, "serving queue is full");
+        r->ticket = S.next_ticket++;
+        *ticket = r->ticket;
+        r->submitted = clk::now();
+        S.pending.push_back(std::move(r));
+        S.cv.notify_all();
+        return DQJ_OK;
+    });
 }
 
 dqj_status dqj_serve_policy(dqj_ctx *ctx, int32_t policy)
 {
-    if (!ctx) return fail(DQJ_ERR_INVALID, "ctx is NULL");
-    if (policy != DQJ_SERVE_FIFO && policy != DQJ_SERVE_SHORTEST)
-        return fail(DQJ_ERR_INVALID, "policy must be DQJ_SERVE_FIFO or DQJ_SERVE_SHORTEST");
-    ctx->serve_policy.store(policy, std::memory_order_relaxed);
-    return DQJ_OK;
+    return dqj::guarded([&]() -> dqj_status {
+        if (!ctx) return fail(DQJ_ERR_INVALID, "ctx is NULL");
+        if (policy != DQJ_SERVE_FIFO && policy != DQJ_SERVE_SHORTEST)
+            return fail(DQJ_ERR_INVALID, "policy must be DQJ_SERVE_FIFO or DQJ_SERVE_SHORTEST");
+        ctx->serve_policy.store(policy, std::memory_order_relaxed);
+        return DQJ_OK;
+    });
 }
 
 dqj_status dqj_serve_stats(dqj_ctx *ctx, int64_t *out)
 {
-    if (!ctx || !out) return fail(DQJ_ERR_INVALID, "ctx or out is NULL");
-    for (int i = 0; i < DQJ_NSERVE_STATS; ++i) out[i] = 0;
-    if (!ctx->serve) return DQJ_OK;
-    ServeState &S = *ctx->serve;
-    std::lock_guard<std::mutex> lk(S.mu);
-    S.backend->launch_counts(out[0], out[1]);
-    out[2] = S.n_packed;
-    out[3] = S.n_plain;
-    out[4] = S.n_batches;
-    out[5] = S.admit_ns;
-    out[6] = S.n_completed;
-    out[7] = S.n_loops;
-    return DQJ_OK;
+    return dqj::guarded([&]() -> dqj_status {
+        if (!ctx || !out) return fail(DQJ_ERR_INVALID, "ctx or out is NULL");
+        for (int i = 0; i < DQJ_NSERVE_STATS; ++i) out[i] = 0;
+        if (!ctx->serve) return DQJ_OK;
+        ServeState &S = *ctx->serve;
+        std::lock_guard<std::mutex> lk(S.mu);
+        S.backend->launch_counts(out[0], out[1]);
+        out[2] = S.n_packed;
+        out[3] = S.n_plain;
+        out[4] = S.n_batches;
+        out[5] = S.admit_ns;
+        out[6] = S.n_completed;
+        out[7] = S.n_loops;
+        return DQJ_OK;
+    });
 }
 
 dqj_status dqj_poll(dqj_ctx *ctx, dqj_ticket ticket, int *done, dqj_status *result)
 {
-    if (!ctx || !done || !result) return fail(DQJ_ERR_INVALID, "ctx, done or result is NULL");
-    if (!ctx->serve) return fail(DQJ_ERR_NOT_FOUND, "unknown ticket");
-    ServeState &S = *ctx->serve;
-    std::lock_guard<std::mutex> lk(S.mu);
-    auto f = S.finished.find(ticket);
-    if (f != S.finished.end()) {
-        *done = 1;
-        *result = f->second;
-        S.finished.erase(f);
-        return DQJ_OK;
-    }
-    if (S.active.count(ticket)) {
-        *done = 0;
-        return DQJ_OK;
-    }
-    for (auto &r : S.pending)
-        if (r->ticket == ticket) {
+    return dqj::guarded([&]() -> dqj_status {
+        if (!ctx || !done || !result) return fail(DQJ_ERR_INVALID, "ctx, done or result is NULL");
+        if (!ctx->serve) return fail(DQJ_ERR_NOT_FOUND, "unknown ticket");
+        ServeState &S = *ctx->serve;
+        std::lock_guard<std::mutex> lk(S.mu);
+        auto f = S.finished.find(ticket);
+        if (f != S.finished.end()) {
+            *done = 1;
+            *result = f->second;
+            S.finished.erase(f);
+            return DQJ_OK;
+        }
+        if (S.active.count(ticket)) {
             *done = 0;
             return DQJ_OK;
         }
-    return fail(DQJ_ERR_NOT_FOUND, "unknown or already consumed ticket");
+        for (auto &r : S.pending)
+            if (r->ticket == ticket) {
+                *done = 0;
+                return DQJ_OK;
+            }
+        return fail(DQJ_ERR_NOT_FOUND, "unknown or already consumed ticket");
+    });
 }
 
 dqj_status dqj_destroy(dqj_ctx *ctx)
 {
-    if (!ctx) return fail(DQJ_ERR_INVALID, "ctx is NULL");
-    const bool device_ctx = ctx->device != DQJ_DEVICE_MOCK;
-    dqj_status result = DQJ_OK;
-    if (ctx->serve) {
-        ServeState &S = *ctx->serve;
-        const int64_t timeout_ms = env_int("DQJ_DESTROY_TIMEOUT_MS", 10000);
-        {
-            std::unique_lock<std::mutex> lk(S.mu);
-            S.draining = true;
-            for (auto &r : S.pending) S.finished[r->ticket] = DQJ_ERR_CANCELLED;
-            S.pending.clear();
-            S.cv.notify_all();
-            S.cv.wait_for(lk, std::chrono::milliseconds(timeout_ms), [&] { return S.active.empty(); });
-            S.stop = true;
-            S.cv.notify_all();
+    return dqj::guarded([&]() -> dqj_status {
+        if (!ctx) return fail(DQJ_ERR_INVALID, "ctx is NULL");
+        const bool device_ctx = ctx->device != DQJ_DEVICE_MOCK;
+        dqj_status result = DQJ_OK;
+        if (ctx->serve) {
+            ServeState &S = *ctx->serve;
+            const int64_t timeout_ms = env_int("DQJ_DESTROY_TIMEOUT_MS", 10000);
+            {
+                std::unique_lock<std::mutex> lk(S.mu);
+                S.draining = true;
+                for (auto &r : S.pending) S.finished[r->ticket] = DQJ_ERR_CANCELLED;
+                S.pending.clear();
+                S.cv.notify_all();
+                S.cv.wait_for(lk, std::chrono::milliseconds(timeout_ms), [&] { return S.active.empty(); });
+                S.stop = true;
+                S.cv.notify_all();
+            }
+            S.thr.join();
+            result = S.backend->shutdown(S.active.empty() ? timeout_ms : 0);
+            if (!S.active.empty() && result == DQJ_OK)
+                result = fail(DQJ_ERR_TIMEOUT, "requests still running when the context was destroyed");
+            if (result == DQJ_OK || ctx->device == DQJ_DEVICE_MOCK) {
+                for (auto &kv : S.active) S.backend->release(*kv.second);
+                delete ctx->serve;
+                ctx->serve = nullptr;
+            } else {
+                // the device may still be using the requests' memory: leak it rather than free it under the kernel
+                ctx->serve = nullptr;
+            }
         }
-        S.thr.join();
-        result = S.backend->shutdown(S.active.empty() ? timeout_ms : 0);
-        if (!S.active.empty() && result == DQJ_OK)
-            result = fail(DQJ_ERR_TIMEOUT, "requests still running when the context was destroyed");
-        if (result == DQJ_OK || ctx->device == DQJ_DEVICE_MOCK) {
-            for (auto &kv : S.active) S.backend->release(*kv.second);
-            delete ctx->serve;
-            ctx->serve = nullptr;
-        } else {
-            // the device may still be using the requests' memory: leak it rather than free it under the kernel
-            ctx->serve = nullptr;
+        if (ctx->device != DQJ_DEVICE_MOCK) {
+            cudaSetDevice(ctx->device);
+            if (ctx->done_capture)  // the last render was captured in a graph: its event is a graph node
+                cudaDeviceSynchronize();
+            else if (ctx->done_ev)
+                cudaEventSynchronize(ctx->done_ev);
+            if (ctx->host_stream) cudaStreamSynchronize(ctx->host_stream);
+            if (ctx->host_copy_stream) cudaStreamSynchronize(ctx->host_copy_stream);
+            scratch_free(ctx->scratch);
+            for (int b = 0; b < 2; ++b) {
+                if (ctx->host_planes[b]) cudaFree(ctx->host_planes[b]);
+                if (ctx->host_rendered[b]) cudaEventDestroy(ctx->host_rendered[b]);
+                if (ctx->host_copied[b]) cudaEventDestroy(ctx->host_copied[b]);
+            }
+            if (ctx->vox_scratch) cudaFree(ctx->vox_scratch);
+            if (ctx->host_stream) cudaStreamDestroy(ctx->host_stream);
+            if (ctx->host_copy_stream) cudaStreamDestroy(ctx->host_copy_stream);
+            if (ctx->done_ev) cudaEventDestroy(ctx->done_ev);
+            for (auto &v : ctx->ev)
+                if (v) cudaEventDestroy(v);
+            ctx->ev.clear();
         }
-    }
-    if (ctx->device != DQJ_DEVICE_MOCK) {
-        cudaSetDevice(ctx->device);
-        if (ctx->done_capture)  // the last render was captured in a graph: its event is a graph node
-            cudaDeviceSynchronize();
-        else if (ctx->done_ev)
-            cudaEventSynchronize(ctx->done_ev);
-        if (ctx->host_stream) cudaStreamSynchronize(ctx->host_stream);
-        if (ctx->host_copy_stream) cudaStreamSynchronize(ctx->host_copy_stream);
-        scratch_free(ctx->scratch);
-        for (int b = 0; b < 2; ++b) {
-            if (ctx->host_planes[b]) cudaFree(ctx->host_planes[b]);
-            if (ctx->host_rendered[b]) cudaEventDestroy(ctx->host_rendered[b]);
-            if (ctx->host_copied[b]) cudaEventDestroy(ctx->host_copied[b]);
-        }
-        if (ctx->vox_scratch) cudaFree(ctx->vox_scratch);
-        if (ctx->host_stream) cudaStreamDestroy(ctx->host_stream);
-        if (ctx->host_copy_stream) cudaStreamDestroy(ctx->host_copy_stream);
-        if (ctx->done_ev) cudaEventDestroy(ctx->done_ev);
-        for (auto &v : ctx->ev)
-            if (v) cudaEventDestroy(v);
-        ctx->ev.clear();
-    }
-    delete ctx;
-    if (device_ctx) (void)cudaGetLastError();  // teardown leaves no error behind for the caller
-    return result;
+        delete ctx;
+        if (device_ctx) (void)cudaGetLastError();  // teardown leaves no error behind for the caller
+        return result;
+    });
 }
 
 }  // extern "C"

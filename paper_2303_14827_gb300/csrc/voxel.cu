@@ -314,50 +314,52 @@ using namespace dqj;
 extern "C" dqj_status dqj_voxelize(dqj_ctx *ctx, const dqj_params *p, int32_t grid_n, uint8_t *occupancy,
                                    uint16_t *counts, int64_t *stats, void *cuda_stream)
 {
-    if (!ctx) return fail(DQJ_ERR_INVALID, "ctx is NULL");
-    dqj_status s = validate(p);
-    if (s != DQJ_OK) return s;
-    if (grid_n < 1 || grid_n > DQJ_VOXEL_MAX_GRID)
-        return fail(DQJ_ERR_INVALID, "grid_n must be in 1.." + std::to_string(DQJ_VOXEL_MAX_GRID));
-    if (counts && (reinterpret_cast<uintptr_t>(counts) & 1u)) return fail(DQJ_ERR_INVALID, "counts must be 2-byte aligned");
-    if (stats && (reinterpret_cast<uintptr_t>(stats) & 7u)) return fail(DQJ_ERR_INVALID, "stats must be 8-byte aligned");
-    if (!occupancy && !counts) return fail(DQJ_ERR_INVALID, "occupancy and counts are both NULL");
-    if (ctx->device == DQJ_DEVICE_MOCK) return fail(DQJ_ERR_INVALID, "a mock context cannot voxelize");
-    std::lock_guard<std::mutex> lk(ctx->mu);
-    cudaError_t e = cudaSetDevice(ctx->device);
-    if (e != cudaSuccess) return cuda_fail(e, "voxelize: cudaSetDevice");
-    const uint64_t cells = (uint64_t)grid_n * (uint64_t)grid_n * (uint64_t)grid_n;
-    const bool re = p->precision == DQJ_FP32_RECHECK;
-    const uint64_t qcap = re ? std::min<uint64_t>(cells, 1ull << 24) : 0;
-    const size_t need = 256 + qcap * sizeof(uint32_t);
-    if (ctx->vox_bytes < need) {
-        e = cudaDeviceSynchronize();
-        if (e != cudaSuccess) return cuda_fail(e, "voxelize: synchronize");
-        if (ctx->vox_scratch) cudaFree(ctx->vox_scratch);
-        ctx->vox_scratch = nullptr;
-        ctx->vox_bytes = 0;
-        e = cudaMalloc(&ctx->vox_scratch, need);
-        if (e != cudaSuccess) return cuda_fail(e, "voxelize: cudaMalloc");
-        ctx->vox_bytes = need;
-    }
-    FrameDesc fd;
-    derive_frame(*p, fd, 8, 8);
-    VoxelArgs va{};
-    va.g = grid_n;
-    va.segs_per_row = (uint32_t)((grid_n + 31) / 32);  // 32 x 2 segments of the FP32 kernel
-    va.nsegs = (uint64_t)grid_n * (uint64_t)((grid_n + 1) / 2) * va.segs_per_row;
-    va.occ = occupancy;
-    va.count = counts;
-    va.ctr = static_cast<Counters *>(ctx->vox_scratch);
-    va.queue = reinterpret_cast<uint32_t *>(static_cast<char *>(ctx->vox_scratch) + 256);
-    va.queue_cap = (uint32_t)qcap;
-    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-    e = cudaStreamWaitEvent(st, ctx->done_ev, 0);
-    if (e == cudaSuccess) e = cudaMemsetAsync(va.ctr, 0, sizeof(Counters), st);
-    if (e == cudaSuccess) e = launch_voxels(fd, va, st, ctx->num_sms);
-    if (e == cudaSuccess && stats)
-        e = cudaMemcpyAsync(stats, va.ctr->stats, DQJ_NSTATS * sizeof(int64_t), cudaMemcpyDeviceToDevice, st);
-    if (e == cudaSuccess) e = cudaEventRecord(ctx->done_ev, st);
-    if (e != cudaSuccess) return cuda_fail(e, "voxelize: launch");
-    return DQJ_OK;
+    return dqj::guarded([&]() -> dqj_status {
+        if (!ctx) return fail(DQJ_ERR_INVALID, "ctx is NULL");
+        dqj_status s = validate(p);
+        if (s != DQJ_OK) return s;
+        if (grid_n < 1 || grid_n > DQJ_VOXEL_MAX_GRID)
+            return fail(DQJ_ERR_INVALID, "grid_n must be in 1.." + std::to_string(DQJ_VOXEL_MAX_GRID));
+        if (counts && (reinterpret_cast<uintptr_t>(counts) & 1u)) return fail(DQJ_ERR_INVALID, "counts must be 2-byte aligned");
+        if (stats && (reinterpret_cast<uintptr_t>(stats) & 7u)) return fail(DQJ_ERR_INVALID, "stats must be 8-byte aligned");
+        if (!occupancy && !counts) return fail(DQJ_ERR_INVALID, "occupancy and counts are both NULL");
+        if (ctx->device == DQJ_DEVICE_MOCK) return fail(DQJ_ERR_INVALID, "a mock context cannot voxelize");
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        cudaError_t e = cudaSetDevice(ctx->device);
+        if (e != cudaSuccess) return cuda_fail(e, "voxelize: cudaSetDevice");
+        const uint64_t cells = (uint64_t)grid_n * (uint64_t)grid_n * (uint64_t)grid_n;
+        const bool re = p->precision == DQJ_FP32_RECHECK;
+        const uint64_t qcap = re ? std::min<uint64_t>(cells, 1ull << 24) : 0;
+        const size_t need = 256 + qcap * sizeof(uint32_t);
+        if (ctx->vox_bytes < need) {
+            e = cudaDeviceSynchronize();
+            if (e != cudaSuccess) return cuda_fail(e, "voxelize: synchronize");
+            if (ctx->vox_scratch) cudaFree(ctx->vox_scratch);
+            ctx->vox_scratch = nullptr;
+            ctx->vox_bytes = 0;
+            e = cudaMalloc(&ctx->vox_scratch, need);
+            if (e != cudaSuccess) return cuda_fail(e, "voxelize: cudaMalloc");
+            ctx->vox_bytes = need;
+        }
+        FrameDesc fd;
+        derive_frame(*p, fd, 8, 8);
+        VoxelArgs va{};
+        va.g = grid_n;
+        va.segs_per_row = (uint32_t)((grid_n + 31) / 32);  // 32 x 2 segments of the FP32 kernel
+        va.nsegs = (uint64_t)grid_n * (uint64_t)((grid_n + 1) / 2) * va.segs_per_row;
+        va.occ = occupancy;
+        va.count = counts;
+        va.ctr = static_cast<Counters *>(ctx->vox_scratch);
+        va.queue = reinterpret_cast<uint32_t *>(static_cast<char *>(ctx->vox_scratch) + 256);
+        va.queue_cap = (uint32_t)qcap;
+        cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+        e = cudaStreamWaitEvent(st, ctx->done_ev, 0);
+        if (e == cudaSuccess) e = cudaMemsetAsync(va.ctr, 0, sizeof(Counters), st);
+        if (e == cudaSuccess) e = launch_voxels(fd, va, st, ctx->num_sms);
+        if (e == cudaSuccess && stats)
+            e = cudaMemcpyAsync(stats, va.ctr->stats, DQJ_NSTATS * sizeof(int64_t), cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->done_ev, st);
+        if (e != cudaSuccess) return cuda_fail(e, "voxelize: launch");
+        return DQJ_OK;
+    });
 }

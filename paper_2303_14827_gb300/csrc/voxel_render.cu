@@ -230,42 +230,44 @@ using namespace dqj;
 extern "C" dqj_status dqj_render_voxels(dqj_ctx *ctx, const dqj_params *p, int32_t grid_n, const uint8_t *occupancy,
                                         const dqj_outputs *out, void *cuda_stream)
 {
-    if (!ctx) return fail(DQJ_ERR_INVALID, "ctx is NULL");
-    dqj_status s = validate(p);
-    if (s != DQJ_OK) return s;
-    if (grid_n < 1 || grid_n > DQJ_VOXEL_MAX_GRID)
-        return fail(DQJ_ERR_INVALID, "grid_n must be in 1.." + std::to_string(DQJ_VOXEL_MAX_GRID));
-    if (!occupancy) return fail(DQJ_ERR_INVALID, "occupancy is NULL");
-    s = check_outputs(*p, out);
-    if (s != DQJ_OK) return s;
-    if (ctx->device == DQJ_DEVICE_MOCK) return fail(DQJ_ERR_INVALID, "a mock context cannot render voxels");
-    std::lock_guard<std::mutex> lk(ctx->mu);
-    cudaError_t e = cudaSetDevice(ctx->device);
-    if (e != cudaSuccess) return cuda_fail(e, "render_voxels: cudaSetDevice");
-    FrameDesc fd;
-    derive_frame(*p, fd, 8, 8);
-    fd.pitch = out->pitch_px;
-    fd.iter = out->iter;
-    fd.depth = out->depth;
-    fd.normal = out->normal;
-    fd.rgba = out->rgba;
-    GridGeom geo;
-    for (int a = 0; a < 3; ++a) {
-        const double ext = p->box_max[a] - p->box_min[a];
-        geo.size[a] = ext / (double)grid_n;
-        geo.inv_size[a] = (double)grid_n / ext;
-        geo.lo_e[a] = p->box_min[a] - p->eye[a];
-        geo.hi_e[a] = p->box_max[a] - p->eye[a];
-    }
-    // the pinhole map of the FP64 camera, 2 (x + 0.5) / W - 1 and
-    // 1 - 2 (y + 0.5) / H scaled by tan(fov_y / 2) (and the aspect for x)
-    geo.sxa = 2.0 * fd.d.th * fd.d.aspect / (double)p->width;
-    geo.sxb = -fd.d.th * fd.d.aspect;
-    geo.sya = -2.0 * fd.d.th / (double)p->height;
-    geo.syb = fd.d.th;
-    const dim3 grid((unsigned)((p->width + kVrTileW - 1) / kVrTileW), (unsigned)((p->height + kVrTileH - 1) / kVrTileH));
-    voxel_render_kernel<<<grid, kBlock, 0, static_cast<cudaStream_t>(cuda_stream)>>>(fd, occupancy, grid_n, geo);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "render_voxels: launch");
-    return DQJ_OK;
+    return dqj::guarded([&]() -> dqj_status {
+        if (!ctx) return fail(DQJ_ERR_INVALID, "ctx is NULL");
+        dqj_status s = validate(p);
+        if (s != DQJ_OK) return s;
+        if (grid_n < 1 || grid_n > DQJ_VOXEL_MAX_GRID)
+            return fail(DQJ_ERR_INVALID, "grid_n must be in 1.." + std::to_string(DQJ_VOXEL_MAX_GRID));
+        if (!occupancy) return fail(DQJ_ERR_INVALID, "occupancy is NULL");
+        s = check_outputs(*p, out);
+        if (s != DQJ_OK) return s;
+        if (ctx->device == DQJ_DEVICE_MOCK) return fail(DQJ_ERR_INVALID, "a mock context cannot render voxels");
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        cudaError_t e = cudaSetDevice(ctx->device);
+        if (e != cudaSuccess) return cuda_fail(e, "render_voxels: cudaSetDevice");
+        FrameDesc fd;
+        derive_frame(*p, fd, 8, 8);
+        fd.pitch = out->pitch_px;
+        fd.iter = out->iter;
+        fd.depth = out->depth;
+        fd.normal = out->normal;
+        fd.rgba = out->rgba;
+        GridGeom geo;
+        for (int a = 0; a < 3; ++a) {
+            const double ext = p->box_max[a] - p->box_min[a];
+            geo.size[a] = ext / (double)grid_n;
+            geo.inv_size[a] = (double)grid_n / ext;
+            geo.lo_e[a] = p->box_min[a] - p->eye[a];
+            geo.hi_e[a] = p->box_max[a] - p->eye[a];
+        }
+        // the pinhole map of the FP64 camera, 2 (x + 0.5) / W - 1 and
+        // 1 - 2 (y + 0.5) / H scaled by tan(fov_y / 2) (and the aspect for x)
+        geo.sxa = 2.0 * fd.d.th * fd.d.aspect / (double)p->width;
+        geo.sxb = -fd.d.th * fd.d.aspect;
+        geo.sya = -2.0 * fd.d.th / (double)p->height;
+        geo.syb = fd.d.th;
+        const dim3 grid((unsigned)((p->width + kVrTileW - 1) / kVrTileW), (unsigned)((p->height + kVrTileH - 1) / kVrTileH));
+        voxel_render_kernel<<<grid, kBlock, 0, static_cast<cudaStream_t>(cuda_stream)>>>(fd, occupancy, grid_n, geo);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "render_voxels: launch");
+        return DQJ_OK;
+    });
 }

@@ -103,6 +103,38 @@ def test_injected_allocation_failure(mock_env):
     binding.dqj_destroy(ctx)
 
 
+def test_host_exception_at_serve_start_becomes_nomem(mock_env):
+    # no C++ exception crosses the C ABI: a host allocation that fails inside
+    # dqj_submit comes back as DQJ_ERR_NOMEM with a message
+    mock_env.setenv("DQJ_MOCK_FAIL", "throw_start")
+    ctx = binding.dqj_create(MOCK)
+    with pytest.raises(binding.DqjError) as ei:
+        binding.dqj_submit(ctx, scenes.default_scene(width=16, height=16), binding.make_outputs(pitch_px=16))
+    assert ei.value.status == binding.DQJ_ERR_NOMEM and "allocation" in binding.last_error()
+    binding.dqj_destroy(ctx)
+
+
+def test_host_exception_in_the_scheduler_thread(mock_env):
+    # the scheduler thread survives a throwing admission: the admitted request
+    # stays unfinished (its device work might still run), queued ones end with
+    # DQJ_ERR_NOMEM, new submits are refused, and destroy reports TIMEOUT
+    mock_env.setenv("DQJ_MOCK_FAIL", "throw_admit")
+    mock_env.setenv("DQJ_DESTROY_TIMEOUT_MS", "200")
+    s = scenes.default_scene(width=64, height=64)
+    ctx = binding.dqj_create(MOCK, mem_budget_bytes=int(footprint(s) * 1.5))
+    tickets = [binding.dqj_submit(ctx, s, binding.make_outputs(pitch_px=64)) for _ in range(3)]
+    time.sleep(0.05)
+    states = [binding.dqj_poll(ctx, t) for t in tickets]
+    assert states[0] == (False, 0)
+    assert all(st == (True, binding.DQJ_ERR_NOMEM) for st in states[1:]), states
+    with pytest.raises(binding.DqjError) as ei:
+        binding.dqj_submit(ctx, s, binding.make_outputs(pitch_px=64))
+    assert ei.value.status == binding.DQJ_ERR_NOMEM
+    with pytest.raises(binding.DqjError) as ei:
+        binding.dqj_destroy(ctx)
+    assert ei.value.status == binding.DQJ_ERR_TIMEOUT
+
+
 def test_never_completing_device_times_out_at_destroy(mock_env):
     mock_env.setenv("DQJ_MOCK_FAIL", "hang")
     mock_env.setenv("DQJ_DESTROY_TIMEOUT_MS", "200")
