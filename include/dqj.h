@@ -90,7 +90,8 @@ enum {
  * request, default 1000) and DQJ_MOCK_FAIL ("nomem": every admission fails,
  * "hang": no request ever completes, "throw_start" / "throw_admit": a host
  * allocation fails while serving starts / while a batch is admitted) from the
- * environment when serving starts. */
+ * environment when serving starts.  It loads a tile cache written for device
+ * "unknown" with 0 SMs (dqj_tile_shape then reports its entries). */
 #define DQJ_DEVICE_MOCK (-1)
 
 /* Per-context configuration for dqj_create. */

@@ -532,7 +532,9 @@ dqj_status dqj_create(const dqj_config *cfg, dqj_ctx **out)
             if (!ctx) return fail(DQJ_ERR_NOMEM, "create: out of host memory");
             ctx->device = DQJ_DEVICE_MOCK;
             ctx->cfg = c;
+            if (c.autotune_cache) ctx->cache_path = c.autotune_cache;
             ctx->cfg.autotune_cache = nullptr;
+            load_tile_cache(ctx);  // a cache written for device "unknown" with 0 SMs applies
             *out = ctx;
             return DQJ_OK;
         }

@@ -168,3 +168,31 @@ def test_render_host_batch_argument_errors():
                                                     binding.ctypes.byref(o), -1) != binding.DQJ_OK
     finally:
         binding.dqj_destroy(ctx)
+
+
+def test_tile_cache_parsing_on_a_mock_context(tmp_path):
+    # the cache loader keeps valid entries and ignores malformed or inconsistent
+    # ones (a mock context has device name "unknown" and 0 SMs)
+    path = tmp_path / "tiles.json"
+    path.write_text('{"device": "unknown", "sms": 0, "entries": [[1, 0, 0, 16, 4], [1, 1, 0, 9, 9], '
+                    '[1, 9, 0, 8, 8], [0, 2, 1, 32, 1], [1, 3, 3, 64, 1], [x, y], [1, 2, 2, 4'
+                    '}')
+    ctx = binding.dqj_create(-1, autotune_cache=str(path))
+    try:
+        def shape(w, h, mi, precision=scenes.PRECISION_FP32):
+            return binding.dqj_tile_shape(ctx, scenes.default_scene(width=w, height=h, max_iter=mi,
+                                                                    precision=precision))
+        assert shape(256, 256, 12) == (1, 16, 4)        # class 0, bucket 0: from the cache
+        assert shape(512, 512, 12) == (1, 8, 8)         # 9 x 9 is not a 64-ray tile: default
+        assert shape(1024, 1024, 16, scenes.PRECISION_FP64) == (0, 32, 1)
+        assert shape(1920, 1080, 32) == (1, 64, 1)
+        assert shape(1024, 1024, 24) == (1, 8, 8)       # truncated entry ignored
+    finally:
+        binding.dqj_destroy(ctx)
+    wrong = tmp_path / "other.json"
+    wrong.write_text('{"device": "some GPU", "sms": 152, "entries": [[1, 0, 0, 16, 4]]}')
+    ctx = binding.dqj_create(-1, autotune_cache=str(wrong))
+    try:  # a cache of another device is not used
+        assert binding.dqj_tile_shape(ctx, scenes.default_scene(width=256, height=256)) == (1, 8, 8)
+    finally:
+        binding.dqj_destroy(ctx)
