@@ -122,7 +122,12 @@ def test_host_exception_in_the_scheduler_thread(mock_env):
     mock_env.setenv("DQJ_DESTROY_TIMEOUT_MS", "200")
     s = scenes.default_scene(width=64, height=64)
     ctx = binding.dqj_create(MOCK, mem_budget_bytes=int(footprint(s) * 1.5))
-    tickets = [binding.dqj_submit(ctx, s, binding.make_outputs(pitch_px=64)) for _ in range(3)]
+    tickets = [binding.dqj_submit(ctx, s, binding.make_outputs(pitch_px=64))]
+    for _ in range(2):  # queued behind the first, or refused once the thread has stopped
+        try:
+            tickets.append(binding.dqj_submit(ctx, s, binding.make_outputs(pitch_px=64)))
+        except binding.DqjError as e:
+            assert e.status == binding.DQJ_ERR_NOMEM
     time.sleep(0.05)
     states = [binding.dqj_poll(ctx, t) for t in tickets]
     assert states[0] == (False, 0)
