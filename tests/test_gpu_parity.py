@@ -216,3 +216,20 @@ def test_render_host_batch_equals_device_render(rdr):
     bad = [frames[0], dict(frames[1], max_iter=0)]
     with pytest.raises(binding.DqjError):
         binding.dqj_render_host_batch(rdr.ctx, bad, [binding.outputs_of(o) for o in host[:2]])
+
+
+def test_render_host_single_frame_pageable_and_partial_planes(rdr):
+    # dqj_render_host into ordinary (pageable) host memory, only two planes
+    # requested: they equal the device render; the others are not touched
+    import torch
+    s = scenes.default_scene(width=80, height=60, max_iter=14)
+    w, h = s["width"], s["height"]
+    o = {"iter": None, "normal": None,
+         "depth": torch.zeros((h, w), dtype=torch.float32),
+         "rgba": torch.zeros((h, w, 4), dtype=torch.uint8), "stats": None, "pitch_px": w}
+    binding.dqj_render_host(rdr.ctx, s, binding.outputs_of(o))
+    ref = rdr.render(s)
+    assert np.array_equal(o["depth"].numpy(), ref["depth"][:, :w].cpu().numpy())
+    assert np.array_equal(o["rgba"].numpy(), ref["rgba"][:, :w].cpu().numpy())
+    with pytest.raises(binding.DqjError):
+        binding.dqj_render_host(rdr.ctx, dict(s, width=0), binding.outputs_of(o))
