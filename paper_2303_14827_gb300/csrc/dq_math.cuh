@@ -129,6 +129,52 @@ __device__ __forceinline__ int classify_lockstep(T (&z)[8], const FrameT<T> &F, 
     return cnt >= max_iter ? 0 : cnt + 1;
 }
 
+// The modulus of zeta given its sp = r1^2 + r2^2 + r3^2: the tail of dq_iter.
+template <typename T, int MOD>
+__device__ __forceinline__ T modulus_sp(const T (&z)[8], T sp)
+{
+    T x = dfma(z[0], z[0], sp);
+    if (MOD == 0) {
+        x = dfma(z[4], z[4], x);
+        x = dfma(z[5], z[5], x);
+        x = dfma(z[6], z[6], x);
+        x = dfma(z[7], z[7], x);
+    }
+    return x;
+}
+
+// classify_lockstep for a sample given by its first iterate zeta_1 (the FP32
+// march forms zeta_1 directly, see first_iterate_coeffs): step 1 tests
+// modulus(zeta_1), the remaining max_iter - 1 steps iterate from zeta_1.
+template <typename T, int SQ, int MOD, bool RECHECK>
+__device__ __forceinline__ int classify_lockstep_it1(T (&z)[8], const FrameT<T> &F, int max_iter, bool part,
+                                                     bool &marginal)
+{
+    bool alive = part;
+    T sp = dq_sp<T>(z);
+    T m = modulus_sp<T, MOD>(z, sp);
+    bool mg = RECHECK && alive && fabs(m - F.R2) <= F.margin;
+    alive = alive && (m <= F.R2);
+    int cnt = alive ? 1 : 0;
+    T w[8];
+    if (__any_sync(0xffffffffu, alive)) {
+        for (int n = 1; n < max_iter; n += 2) {
+            m = dq_iter<T, SQ, MOD>(z, w, sp, F.c);
+            if (RECHECK) mg = mg || (alive && fabs(m - F.R2) <= F.margin);
+            alive = alive && (m <= F.R2);
+            cnt += alive ? 1 : 0;
+            if (!__any_sync(0xffffffffu, alive) || n + 1 >= max_iter) break;
+            m = dq_iter<T, SQ, MOD>(w, z, sp, F.c);
+            if (RECHECK) mg = mg || (alive && fabs(m - F.R2) <= F.margin);
+            alive = alive && (m <= F.R2);
+            cnt += alive ? 1 : 0;
+            if (!__any_sync(0xffffffffu, alive)) break;
+        }
+    }
+    marginal = mg;
+    return cnt >= max_iter ? 0 : cnt + 1;
+}
+
 // Scalar (per-thread) classification with early exit, for FP64 rechecks and
 // re-renders.  Same return convention.
 // Scalar form of dq_iter2_axis_first: the first step of a sample whose
@@ -192,6 +238,117 @@ __device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(
 __device__ __forceinline__ float2 dq_sp2(const float2 (&z)[8])
 {
     return f2fma(z[3], z[3], f2fma(z[2], z[2], f2mul(z[1], z[1])));
+}
+
+// ---------------------------------------------------------------------------
+// First-iterate form of a march sample.  Along a ray the slice point is
+// zeta_0(t) = A + t D (A the slice image of the eye, D = E d), so its first
+// iterate zeta_1(t) = zeta_0(t)^2 + c is a quadratic in t.  With t* = -(A . D)
+// (the parameter where the slice line passes closest to the slice origin;
+// |D| = 1) and A' = A + t* D:
+//     zeta_1 = Q0 + s (Q1 + s Q2),   s = t - t*,
+//     Q0 = A'^2 + c,   Q1 = A' D + D A',   Q2 = D^2
+// (products in the frame's square mode).  Shifting the origin to A' keeps the
+// three terms of the size of zeta_1 near the set instead of |A|^2, so the form
+// rounds like the direct square.  The coefficients are formed once per ray;
+// each sample then costs two FMAs per component instead of forming zeta_0 and
+// squaring it.  Written once over the lane type V (float, or float2 for two
+// rays per lane) so that the scalar and paired kernels round identically.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float vneg(float a) { return -a; }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return f2fma(a, b, c); }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return f2mul(a, b); }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return f2add(a, b); }
+__device__ __forceinline__ float2 vneg(float2 a) { return make_float2(-a.x, -a.y); }
+
+// o = a^2 (Eq. quatsq) for quaternions a[0..3], scalar first
+template <typename V>
+__device__ __forceinline__ void quat_sq_v(const V *a, V *o)
+{
+    const V ta0 = vadd(a[0], a[0]);
+    V q = vmul(a[1], a[1]);
+    q = vfma(a[2], a[2], q);
+    q = vfma(a[3], a[3], q);
+    o[0] = vfma(a[0], a[0], vneg(q));
+    o[1] = vmul(ta0, a[1]);
+    o[2] = vmul(ta0, a[2]);
+    o[3] = vmul(ta0, a[3]);
+}
+
+// o = a b + b a = 2 (a0 b0 - av . bv, a0 bv + b0 av) (the cross products cancel)
+template <typename V>
+__device__ __forceinline__ void quat_sym_v(const V *a, const V *b, V *o)
+{
+    V q = vmul(a[1], b[1]);
+    q = vfma(a[2], b[2], q);
+    q = vfma(a[3], b[3], q);
+    const V r = vfma(a[0], b[0], vneg(q));
+    o[0] = vadd(r, r);
+#pragma unroll
+    for (int i = 1; i < 4; ++i) {
+        const V t = vfma(a[0], b[i], vmul(b[0], a[i]));
+        o[i] = vadd(t, t);
+    }
+}
+
+// o = a^2 in square mode SQ (0 algebraic: (a_r^2, a_r a_d + a_d a_r);
+// 1 component-wise: (a_r^2, a_d^2))
+template <typename V, int SQ>
+__device__ __forceinline__ void dq_sq_v(const V (&a)[8], V (&o)[8])
+{
+    quat_sq_v(a, o);
+    if (SQ == 0)
+        quat_sym_v(a, a + 4, o + 4);
+    else
+        quat_sq_v(a + 4, o + 4);
+}
+
+// o = a b + b a in square mode SQ (the cross term of (a + s b)^2)
+template <typename V, int SQ>
+__device__ __forceinline__ void dq_sym_v(const V (&a)[8], const V (&b)[8], V (&o)[8])
+{
+    quat_sym_v(a, b, o);
+    if (SQ == 0) {
+        V u[4], w[4];
+        quat_sym_v(a, b + 4, u);
+        quat_sym_v(a + 4, b, w);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) o[4 + i] = vadd(u[i], w[i]);
+    } else {
+        quat_sym_v(a + 4, b + 4, o + 4);
+    }
+}
+
+// Coefficients of the first-iterate form of one ray (see above); dot = A . D,
+// so s = t + dot.
+template <typename V, int SQ>
+__device__ __forceinline__ void first_iterate_coeffs(const V (&A)[8], const V (&D)[8], const V (&c)[8], V &dot,
+                                                     V (&Q0)[8], V (&Q1)[8], V (&Q2)[8])
+{
+    V d = vmul(A[0], D[0]);
+#pragma unroll
+    for (int i = 1; i < 8; ++i) d = vfma(A[i], D[i], d);
+    dot = d;
+    const V ts = vneg(d);
+    V Ap[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) Ap[i] = vfma(ts, D[i], A[i]);
+    dq_sq_v<V, SQ>(Ap, Q0);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) Q0[i] = vadd(Q0[i], c[i]);
+    dq_sym_v<V, SQ>(Ap, D, Q1);
+    dq_sq_v<V, SQ>(D, Q2);
+}
+
+// zeta_1 at s: Q0 + s (Q1 + s Q2), components [0, n)
+template <typename V, int n>
+__device__ __forceinline__ void first_iterate(V s, const V (&Q0)[8], const V (&Q1)[8], const V (&Q2)[8], V (&z)[8])
+{
+#pragma unroll
+    for (int i = 0; i < n; ++i) z[i] = vfma(s, vfma(s, Q2[i], Q1[i]), Q0[i]);
 }
 
 template <int SQ, int MOD>
@@ -262,67 +419,121 @@ __device__ __forceinline__ float2 dq_iter2_axis_first(const float2 (&zi)[8], flo
 // hold the number of steps it stayed bounded (escape count - 1, or max_iter).
 // AXIS: the samples lie in an axis-aligned slice, only z[0..2] are set on entry
 // (components 3..7 are zero) and the first step takes dq_iter2_axis_first.
+// `live` (warp-uniform) is false when the warp's last vote saw no bounded half:
+// then no half is inside.
+// RECHECK: dm returns, per half with a sample, the smallest distance of a
+// tested modulus from R^2, up to and including the escaping one: the sample is
+// marginal when dm <= P.margin_t.  Each later step costs one paired
+// subtraction and a predicated minimum per half; the axis-form first step
+// measures |a - a_c| instead (see PairConsts), for every half alike, so a half
+// without a sample must carry a z whose first step is far outside the band
+// (march2_tile gives it a ray parameter of 1e18: a = +inf).  Without AXIS such
+// a half keeps dm = +inf.
 template <int SQ, int MOD, bool RECHECK, bool AXIS = false>
-__device__ __forceinline__ void classify_lockstep2(float2 (&z)[8], const PairConsts &P, float R2, float margin,
-                                                   int max_iter, bool &aa, bool &ab, int &ca, int &cb, bool &mga,
-                                                   bool &mgb)
+__device__ __forceinline__ void classify_lockstep2(float2 (&z)[8], const PairConsts &P, float R2, int max_iter,
+                                                   bool &aa, bool &ab, int &ca, int &cb, float2 &dm, bool &live)
 {
-    bool ma = false, mb = false;
+    const float inf = __int_as_float(0x7f800000);
+    dm = make_float2(inf, inf);
+    bool v = true;
     int na = 0, nb = 0;
     float2 sp = AXIS ? f2fma(z[2], z[2], f2mul(z[1], z[1])) : dq_sp2(z);
     float2 w[8];
+    // one tested step: escape test, count, and the margin distance while bounded
+    auto test = [&](float2 x) {
+        if (RECHECK) {
+            const float2 u = f2add(x, P.negR2);
+            dm.x = fminf(dm.x, fabsf(u.x));
+            dm.y = fminf(dm.y, fabsf(u.y));
+        }
+        aa = aa && (x.x <= R2);
+        ab = ab && (x.y <= R2);
+        na += aa ? 1 : 0;
+        nb += ab ? 1 : 0;
+    };
     int n0 = 0;
     if constexpr (AXIS) {  // the first trip, peeled so that its first step takes the axis form
         n0 = max_iter;
-        const float2 a = dq_iter2_axis_first(z, w, sp, P);  // thresholds on a, exact (see PairConsts)
-        if (RECHECK) {
-            ma = ma || (aa && a.x >= P.t_mlo && a.x <= P.t_mhi);
-            mb = mb || (ab && a.y >= P.t_mlo && a.y <= P.t_mhi);
+        const float2 a = dq_iter2_axis_first(z, w, sp, P);  // tests on a (see PairConsts)
+        if (RECHECK) {  // a half without a sample must come with a far-away z (see march2_tile)
+            const float2 u = f2add(a, P.neg_ac);
+            dm.x = fabsf(u.x);
+            dm.y = fabsf(u.y);
         }
         aa = aa && (a.x < P.t_esc);
         ab = ab && (a.y < P.t_esc);
         na += aa ? 1 : 0;
         nb += ab ? 1 : 0;
-        if (__any_sync(0xffffffffu, aa || ab) && max_iter > 1) {
-            float2 x = dq_iter2<SQ, MOD>(w, z, sp, P);
-            if (RECHECK) {
-                ma = ma || (aa && fabsf(x.x - R2) <= margin);
-                mb = mb || (ab && fabsf(x.y - R2) <= margin);
-            }
-            aa = aa && (x.x <= R2);
-            ab = ab && (x.y <= R2);
-            na += aa ? 1 : 0;
-            nb += ab ? 1 : 0;
-            if (__any_sync(0xffffffffu, aa || ab)) n0 = 2;
+        v = __any_sync(0xffffffffu, aa || ab);
+        if (v && max_iter > 1) {
+            test(dq_iter2<SQ, MOD>(w, z, sp, P));
+            v = __any_sync(0xffffffffu, aa || ab);
+            if (v) n0 = 2;
         }
     }
     // two steps per trip, z -> w -> z, with the escape test after each
     for (int n = n0; n < max_iter; n += 2) {
-        float2 x = dq_iter2<SQ, MOD>(z, w, sp, P);
-        if (RECHECK) {
-            ma = ma || (aa && fabsf(x.x - R2) <= margin);
-            mb = mb || (ab && fabsf(x.y - R2) <= margin);
-        }
-        aa = aa && (x.x <= R2);
-        ab = ab && (x.y <= R2);
-        na += aa ? 1 : 0;
-        nb += ab ? 1 : 0;
-        if (!__any_sync(0xffffffffu, aa || ab) || n + 1 >= max_iter) break;
-        x = dq_iter2<SQ, MOD>(w, z, sp, P);
-        if (RECHECK) {
-            ma = ma || (aa && fabsf(x.x - R2) <= margin);
-            mb = mb || (ab && fabsf(x.y - R2) <= margin);
-        }
-        aa = aa && (x.x <= R2);
-        ab = ab && (x.y <= R2);
-        na += aa ? 1 : 0;
-        nb += ab ? 1 : 0;
-        if (!__any_sync(0xffffffffu, aa || ab)) break;
+        test(dq_iter2<SQ, MOD>(z, w, sp, P));
+        v = __any_sync(0xffffffffu, aa || ab);
+        if (!v || n + 1 >= max_iter) break;
+        test(dq_iter2<SQ, MOD>(w, z, sp, P));
+        v = __any_sync(0xffffffffu, aa || ab);
+        if (!v) break;
     }
+    live = v;
     ca = na;
     cb = nb;
-    mga = ma;
-    mgb = mb;
+}
+
+// classify_lockstep2 for samples given by their first iterate zeta_1 (the
+// first-iterate form of a general slice, see first_iterate_coeffs): step 1 is
+// the escape test of zeta_1, the remaining max_iter - 1 steps iterate from it.
+// Same outputs and recheck distance as classify_lockstep2.
+template <int SQ, int MOD, bool RECHECK>
+__device__ __forceinline__ void classify_lockstep2_it1(float2 (&z)[8], const PairConsts &P, float R2, int max_iter,
+                                                       bool &aa, bool &ab, int &ca, int &cb, float2 &dm, bool &live)
+{
+    const float inf = __int_as_float(0x7f800000);
+    dm = make_float2(inf, inf);
+    int na = 0, nb = 0;
+    float2 sp = dq_sp2(z);
+    float2 w[8];
+    auto test = [&](float2 x) {
+        if (RECHECK) {
+            const float2 u = f2add(x, P.negR2);
+            dm.x = fminf(dm.x, fabsf(u.x));
+            dm.y = fminf(dm.y, fabsf(u.y));
+        }
+        aa = aa && (x.x <= R2);
+        ab = ab && (x.y <= R2);
+        na += aa ? 1 : 0;
+        nb += ab ? 1 : 0;
+    };
+    {
+        float2 x = f2fma(z[0], z[0], sp);
+        if (MOD == 0) {
+            x = f2fma(z[4], z[4], x);
+            x = f2fma(z[5], z[5], x);
+            x = f2fma(z[6], z[6], x);
+            x = f2fma(z[7], z[7], x);
+        }
+        test(x);
+    }
+    bool v = __any_sync(0xffffffffu, aa || ab);
+    if (v) {
+        // two steps per trip, z -> w -> z, with the escape test after each
+        for (int n = 1; n < max_iter; n += 2) {
+            test(dq_iter2<SQ, MOD>(z, w, sp, P));
+            v = __any_sync(0xffffffffu, aa || ab);
+            if (!v || n + 1 >= max_iter) break;
+            test(dq_iter2<SQ, MOD>(w, z, sp, P));
+            v = __any_sync(0xffffffffu, aa || ab);
+            if (!v) break;
+        }
+    }
+    live = v;
+    ca = na;
+    cb = nb;
 }
 
 }  // namespace dqj

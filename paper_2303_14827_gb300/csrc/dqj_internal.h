@@ -44,11 +44,17 @@ struct PairConsts {
     float2 c[8];
     float2 A[8];
     float2 neg1, neg2;
+    float2 negR2;   // (-R^2, -R^2): modulus - R^2 of both halves in one paired add
+    float2 neg_ac;  // (-a_c, -a_c): centre of the first step's recheck band on a (below)
     // Axis-slice first step: its modulus is a = z0^2 + sp followed by the fixed
     // FMAs with c4..c7 (EUCLID8), a monotone function of a, so its tests are
-    // thresholds on a, found on the host: escape <=> a >= t_esc; recheck margin
-    // <=> t_mlo <= a <= t_mhi.
-    float t_esc, t_mlo, t_mhi, t_pad;
+    // thresholds on a, found on the host: escape <=> a >= t_esc (exact); the
+    // recheck band |modulus - R^2| <= margin is a in [t_mlo, t_mhi].  The paired
+    // kernels test the band as |a - a_c| <= margin_t, and later steps as
+    // |modulus - R^2| <= margin_t, where margin_t >= margin is the smallest
+    // float for which [a_c - margin_t, a_c + margin_t] contains [t_mlo, t_mhi]:
+    // a superset of the exact band by at most a few units in the last place.
+    float t_esc, t_mlo, t_mhi, margin_t;
 };
 
 struct alignas(16) FrameDesc {

@@ -54,16 +54,29 @@ __global__ void __launch_bounds__(kBlock) march_kernel(const __grid_constant__ F
         T D[8];
         slice_dir<T>(F, d, D);
         const T delta = (t_out - t_in) / T(fd.N);
+        // FP32 general slice: the first-iterate form of the paired kernel, same
+        // operations per ray
+        const bool it1 = sizeof(T) == 4 && !fd.axis_slice;
+        T Q0[8], Q1[8], Q2[8], dot = T(0);
+        if constexpr (sizeof(T) == 4)
+            if (it1) first_iterate_coeffs<float, SQ>(F.A, D, F.c, dot, Q0, Q1, Q2);
+        const T s_in = it1 ? (T)vadd((float)t_in, (float)dot) : t_in;
         int esc_max = 0, k_first = -1;
         unsigned iters = 0, samples = 0;
         for (int k = 0; k <= fd.N; ++k) {
             if (!__any_sync(kFull, active)) break;
-            const T t = dfma(T(k), delta, t_in);
             T z[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) z[i] = dfma(t, D[i], F.A[i]);
             bool mg;
-            const int n = classify_lockstep<T, SQ, MOD, RECHECK>(z, F, fd.max_iter, active, mg);
+            int n;
+            if (it1) {
+                if constexpr (sizeof(T) == 4) first_iterate<float, 8>(vfma((float)k, delta, s_in), Q0, Q1, Q2, z);
+                n = classify_lockstep_it1<T, SQ, MOD, RECHECK>(z, F, fd.max_iter, active, mg);
+            } else {
+                const T t = dfma(T(k), delta, t_in);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) z[i] = dfma(t, D[i], F.A[i]);
+                n = classify_lockstep<T, SQ, MOD, RECHECK>(z, F, fd.max_iter, active, mg);
+            }
             if (RECHECK) {
                 const bool push = active && mg;
                 if (warp_push(push, make_int4(y * fd.W + x, k | (kMarchSample << 16), 0, n), sc.queue,
@@ -109,19 +122,32 @@ __global__ void __launch_bounds__(kBlock) march_kernel(const __grid_constant__ F
 // bisection pass, which needs it only for hits.
 // ---------------------------------------------------------------------------
 template <int SQ, int MOD, bool RECHECK, bool AXIS>
-__global__ void __launch_bounds__(kBlock, 5) march2_kernel(const __grid_constant__ FrameDesc fd, const Scratch sc)
+__global__ void __launch_bounds__(kBlock, AXIS ? 5 : 4)  // the general form keeps 24 coefficients per ray pair
+    march2_kernel(const __grid_constant__ FrameDesc fd, const Scratch sc)
 {
+    __shared__ int4 stage[RECHECK ? kBlock / 32 : 1][RECHECK ? kQStage : 1];  // recheck entries, per warp
     const int lane = threadIdx.x & 31;
     const unsigned ntiles = (unsigned)fd.tiles_x * (unsigned)fd.tiles_y;
-    LaneStats st;
     for (;;) {
         unsigned tile = 0;
         if (lane == 0) tile = atomicAdd(&sc.ctr->tile_next, 1u);
         tile = __shfl_sync(kFull, tile, 0);
         if (tile >= ntiles) break;
-        march2_tile<SQ, MOD, RECHECK, AXIS>(fd, fd.p2, sc, tile, st);
+        // counters are added per tile, so none stays live across the march loop
+        LaneStats st;
+        if constexpr (AXIS) {
+            march2_tile<SQ, MOD, RECHECK, AXIS>(fd, fd.p2, sc, tile, st, stage[RECHECK ? threadIdx.x >> 5 : 0]);
+        } else {
+            // the general form takes the pair constants from a copy, as the
+            // serving kernel does: with them read from the parameter bank
+            // the first-iterate setup compiled to a result that differed
+            // from the scalar kernel's and the serving kernel's (up to two
+            // iterations per frame, no pixel changed)
+            PairConsts P = fd.p2;
+            march2_tile<SQ, MOD, RECHECK, AXIS>(fd, P, sc, tile, st, stage[RECHECK ? threadIdx.x >> 5 : 0]);
+        }
+        flush_lane_stats<false>(sc, st, true);
     }
-    flush_lane_stats<RECHECK>(sc, st, true);
 }
 
 // ---------------------------------------------------------------------------
@@ -331,17 +357,22 @@ __global__ void __launch_bounds__(kBlock) fixup_kernel(const __grid_constant__ F
 template <typename T, int SQ, int MOD, bool RECHECK>
 cudaError_t launch_passes(const FrameDesc &fd, const Scratch &sc, cudaStream_t st, int num_sms, cudaEvent_t *ev)
 {
-    static std::atomic<int> g_march{0}, g_march2{0}, g_bisect{0};
+    static std::atomic<int> g_march{0}, g_march2a{0}, g_march2g{0}, g_bisect{0};
     const unsigned ntiles = (unsigned)fd.tiles_x * (unsigned)fd.tiles_y;
     if (ev) cudaEventRecord(ev[0], st);
     if constexpr (sizeof(T) == 4) {
         if (fd.march_variant == 1) {
-            const int cap = num_sms * resident_per_sm(g_march2, march2_kernel<SQ, MOD, RECHECK, false>);
-            const int gm = (int)min((unsigned)cap, (ntiles + 3u) / 4u);
-            if (fd.axis_slice)
+            // a persistent grid per instantiation: the axis and general forms
+            // have different register counts and resident CTAs per SM
+            if (fd.axis_slice) {
+                const int cap = num_sms * resident_per_sm(g_march2a, march2_kernel<SQ, MOD, RECHECK, true>);
+                const int gm = (int)min((unsigned)cap, (ntiles + 3u) / 4u);
                 march2_kernel<SQ, MOD, RECHECK, true><<<gm > 0 ? gm : 1, kBlock, 0, st>>>(fd, sc);
-            else
+            } else {
+                const int cap = num_sms * resident_per_sm(g_march2g, march2_kernel<SQ, MOD, RECHECK, false>);
+                const int gm = (int)min((unsigned)cap, (ntiles + 3u) / 4u);
                 march2_kernel<SQ, MOD, RECHECK, false><<<gm > 0 ? gm : 1, kBlock, 0, st>>>(fd, sc);
+            }
         }
     }
     if (sizeof(T) != 4 || fd.march_variant != 1) {

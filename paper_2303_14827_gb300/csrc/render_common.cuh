@@ -223,72 +223,149 @@ __device__ __forceinline__ void shade_write(const FrameDesc &fd, const FrameT<T>
             make_uchar4(to_u8(v * F.albedo[0]), to_u8(v * F.albedo[1]), to_u8(v * F.albedo[2]), 255);
 }
 
+// Recheck entries of one warp are staged in shared memory and appended to the
+// frame's queue in one block per tile: a single atomic per tile instead of one
+// per round with a marginal sample, which left the warp waiting on the
+// contended queue counter.  kQStage entries per warp; a round adds at most 64.
+constexpr int kQStage = 128;
+// Ray parameter of a half without a sample in the recheck march: its first
+// iterate overflows (modulus +inf) and the later ones are infinite or NaN, so
+// its distance from R^2 never falls within a recheck band.
+constexpr float kFarT = 1e18f;
+
+// Append a warp's staged entries qs[0, qn) to the recheck queue (qn warp-uniform)
+// and count them as rechecks; entries beyond the queue's capacity re-render
+// their pixel in FP64.
+__device__ __forceinline__ void flush_staged(const FrameDesc &fd, const Scratch &sc, const int4 *qs, int qn)
+{
+    const int lane = threadIdx.x & 31;
+    __syncwarp();
+    unsigned base = 0;
+    if (lane == 0) {
+        base = atomicAdd(&sc.ctr->queue_count, (unsigned)qn);
+        atomicAdd(&sc.ctr->stats[4], (unsigned long long)qn);
+    }
+    base = __shfl_sync(kFull, base, 0);
+    for (int i = lane; i < qn; i += 32) {
+        const int4 e = qs[i];
+        if (base + (unsigned)i < sc.queue_cap) {
+            sc.queue[base + i] = e;
+        } else {
+            atomicAdd(&sc.ctr->stats[7], 1ull);
+            mark_dirty(fd, sc, e.x);
+        }
+    }
+    __syncwarp();
+}
+
 // One 64-ray tile of the paired march (see march2_kernel); all 32 lanes call.
+// A lane holds tile slots `lane` and `lane + 32`.  RECHECK: qs is the warp's
+// staging buffer of kQStage entries in shared memory.
 template <int SQ, int MOD, bool RECHECK, bool AXIS = false>
 __device__ __forceinline__ void march2_tile(const FrameDesc &fd, const PairConsts &P, const Scratch &sc, unsigned tile,
-                                            LaneStats &st)
+                                            LaneStats &st, int4 *qs = nullptr)
 {
     const FrameT<float> &F = fd.f;
     const int lane = threadIdx.x & 31;
     const int N = fd.N, max_iter = fd.max_iter;
     const int tx = (int)(tile % (unsigned)fd.tiles_x), ty = (int)(tile / (unsigned)fd.tiles_x);
-    const int sb = lane + 32;
-    const int xa = tx * fd.tile_w + lane % fd.tile_w, ya = ty * fd.tile_h + lane / fd.tile_w;
-    const int xb = tx * fd.tile_w + sb % fd.tile_w, yb = ty * fd.tile_h + sb / fd.tile_w;
-    const bool va = xa < fd.W && ya < fd.H, vb = xb < fd.W && yb < fd.H;
-    float da[3] = {0.f, 0.f, 1.f}, db[3] = {0.f, 0.f, 1.f};
-    float tia = 0.f, toa = 0.f, tib = 0.f, tob = 0.f;
-    const bool boxa = va && camera_clip<float>(F, fd.W, fd.H, xa, ya, da, tia, toa);
-    const bool boxb = vb && camera_clip<float>(F, fd.W, fd.H, xb, yb, db, tib, tob);
-    if (!boxa) tia = toa = 0.f;
-    if (!boxb) tib = tob = 0.f;
-    float2 D[8];
+    // pixel of tile slot s; formed again at the end of the tile rather than kept
+    // live across the march loop (the recheck mode keeps the linear indices)
+    auto px = [&](int slot) { return tx * fd.tile_w + slot % fd.tile_w; };
+    auto py = [&](int slot) { return ty * fd.tile_h + slot / fd.tile_w; };
+    int pixa = 0, pixb = 0;
+    bool acta, actb;
+    // Axis-aligned slice: zeta_0 = A + t D (components 0..2).  Otherwise the
+    // first-iterate form (first_iterate_coeffs): zeta_1 = Q0 + s (Q1 + s Q2),
+    // s = t + dot, with Q0 kept in D and t + dot in tin.
+    float2 D[8], tin, dl;
+    float2 Q1[AXIS ? 1 : 8], Q2[AXIS ? 1 : 8];
     {
+        const int xa = px(lane), ya = py(lane), xb = px(lane + 32), yb = py(lane + 32);
+        if (RECHECK) {
+            pixa = ya * fd.W + xa;
+            pixb = yb * fd.W + xb;
+        }
+        const bool va = xa < fd.W && ya < fd.H, vb = xb < fd.W && yb < fd.H;
+        float da[3] = {0.f, 0.f, 1.f}, db[3] = {0.f, 0.f, 1.f};
+        float tia = 0.f, toa = 0.f, tib = 0.f, tob = 0.f;
+        acta = va && camera_clip<float>(F, fd.W, fd.H, xa, ya, da, tia, toa);
+        actb = vb && camera_clip<float>(F, fd.W, fd.H, xb, yb, db, tib, tob);
+        if (!acta) tia = toa = 0.f;
+        if (!actb) tib = tob = 0.f;
+        dl = make_float2((toa - tia) / (float)N, (tob - tib) / (float)N);
+        if (RECHECK) {  // a half without a ray samples far away: never within the recheck band
+            if (!acta) tia = kFarT;
+            if (!actb) tib = kFarT;
+        }
         float Da[8], Db[8];
         slice_dir<float>(F, da, Da);
         slice_dir<float>(F, db, Db);
 #pragma unroll
         for (int i = 0; i < 8; ++i) D[i] = make_float2(Da[i], Db[i]);
+        tin = make_float2(tia, tib);
+        if constexpr (!AXIS) {
+            float2 dot, Q0[8];
+            first_iterate_coeffs<float2, SQ>(P.A, D, P.c, dot, Q0, Q1, Q2);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) D[i] = Q0[i];
+            tin = f2add(tin, dot);
+        }
     }
-    const float2 tin = make_float2(tia, tib);
-    const float2 dl = make_float2((toa - tia) / (float)N, (tob - tib) / (float)N);
-    bool acta = boxa, actb = boxb;
+    const bool boxa = acta, boxb = actb;
     int suma = 0, sumb = 0, maxa = 0, maxb = 0, kfa = -1, kfb = -1;
+    int qn = 0;  // staged recheck entries (warp-uniform)
     float2 kf = make_float2(0.f, 0.f);
-    for (int k = 0; k <= N; ++k) {
-        if (!__any_sync(kFull, acta || actb)) break;
+    // `more`: some ray of the warp still marches.  It changes only in a round
+    // that found a ray inside, so it is voted on only then.
+    bool more = __any_sync(kFull, acta || actb);
+    for (int k = 0; k <= N && more; ++k) {
         const float2 t = f2fma(kf, dl, tin);
         kf = f2add(kf, make_float2(1.f, 1.f));
         float2 z[8];
-#pragma unroll
-        for (int i = 0; i < (AXIS ? 3 : 8); ++i) z[i] = f2fma(t, D[i], P.A[i]);  // AXIS: the rest are 0
-        bool ina = acta, inb = actb, mga, mgb;
+        bool ina = acta, inb = actb, live;
         int ca, cb;
-        classify_lockstep2<SQ, MOD, RECHECK, AXIS>(z, P, F.R2, F.margin, max_iter, ina, inb, ca, cb, mga, mgb);
-        if (RECHECK) {
-            const bool pa = acta && mga, pb = actb && mgb;
-            if (warp_push(pa, make_int4(ya * fd.W + xa, k | (kMarchSample << 16), 0, ina ? 0 : ca + 1), sc.queue,
-                          sc.queue_cap, &sc.ctr->queue_count)) {
-                atomicAdd(&sc.ctr->stats[7], 1ull);
-                mark_dirty(fd, sc, ya * fd.W + xa);
+        float2 dm;
+        if constexpr (AXIS) {
+#pragma unroll
+            for (int i = 0; i < 3; ++i) z[i] = f2fma(t, D[i], P.A[i]);  // the rest are 0
+            classify_lockstep2<SQ, MOD, RECHECK, true>(z, P, F.R2, max_iter, ina, inb, ca, cb, dm, live);
+        } else {
+            first_iterate<float2, 8>(t, D, Q1, Q2, z);
+            classify_lockstep2_it1<SQ, MOD, RECHECK>(z, P, F.R2, max_iter, ina, inb, ca, cb, dm, live);
+        }
+        if (RECHECK && __any_sync(kFull, fminf(dm.x, dm.y) <= P.margin_t)) {
+            // a marginal sample in this round (rare): stage it
+            const bool pa = acta && dm.x <= P.margin_t, pb = actb && dm.y <= P.margin_t;
+            const unsigned ba = __ballot_sync(kFull, pa), bb = __ballot_sync(kFull, pb);
+            const unsigned below = (1u << lane) - 1u;
+            const int nqa = __popc(ba), nq = nqa + __popc(bb);
+            if (pa) qs[qn + __popc(ba & below)] = make_int4(pixa, k | (kMarchSample << 16), 0, ina ? 0 : ca + 1);
+            if (pb) qs[qn + nqa + __popc(bb & below)] = make_int4(pixb, k | (kMarchSample << 16), 0, inb ? 0 : cb + 1);
+            qn += nq;
+            if (qn > kQStage - 64) {
+                flush_staged(fd, sc, qs, qn);
+                qn = 0;
             }
-            if (warp_push(pb, make_int4(yb * fd.W + xb, k | (kMarchSample << 16), 0, inb ? 0 : cb + 1), sc.queue,
-                          sc.queue_cap, &sc.ctr->queue_count)) {
-                atomicAdd(&sc.ctr->stats[7], 1ull);
-                mark_dirty(fd, sc, yb * fd.W + xb);
-            }
-            st.rechecks += (pa ? 1 : 0) + (pb ? 1 : 0);
         }
         // ina / inb imply acta / actb (they start equal and only clear)
         suma += ca;
         sumb += cb;
         maxa = max(maxa, ca);
         maxb = max(maxb, cb);
-        if (ina) kfa = k;
-        if (inb) kfb = k;
-        acta = acta && !ina;
-        actb = actb && !inb;
+        if (live) {  // some half stayed bounded: those rays are inside at sample k
+            if (ina) kfa = k;
+            if (inb) kfb = k;
+            if (RECHECK) {  // a finished ray samples far away from now on (see above)
+                if (ina) tin.x = kFarT;
+                if (inb) tin.y = kFarT;
+            }
+            acta = acta && !ina;
+            actb = actb && !inb;
+            more = __any_sync(kFull, acta || actb);
+        }
     }
+    if (RECHECK && qn > 0) flush_staged(fd, sc, qs, qn);
     const bool hita = kfa >= 0, hitb = kfb >= 0;
     // iterations = sum of (escape count) over escaped samples + max_iter per inside sample
     //            = sum of bounded steps + number of escaped samples
@@ -296,6 +373,8 @@ __device__ __forceinline__ void march2_tile(const FrameDesc &fd, const PairConst
     st.iters += (boxa ? suma + nesca : 0) + (boxb ? sumb + nescb : 0);
     st.samples += (boxa ? nesca + (hita ? 1 : 0) : 0) + (boxb ? nescb + (hitb ? 1 : 0) : 0);
     st.hits += (hita ? 1 : 0) + (hitb ? 1 : 0);
+    const int xa = px(lane), ya = py(lane), xb = px(lane + 32), yb = py(lane + 32);
+    const bool va = xa < fd.W && ya < fd.H, vb = xb < fd.W && yb < fd.H;
     if (va && !hita) write_miss<float>(fd, xa, ya, boxa ? maxa + 1 : 0);
     if (vb && !hitb) write_miss<float>(fd, xb, yb, boxb ? maxb + 1 : 0);
     warp_push(hita, make_int4(ya * fd.W + xa, kfa, 0, 0), sc.hits, sc.hit_cap, &sc.ctr->hit_count);
@@ -367,10 +446,24 @@ __device__ __forceinline__ void bisect_chunk(const FrameDesc &fd, const Scratch 
     int n_lo = fd.max_iter;
     {
         T z[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) z[i] = dfma(lo, D[i], F.A[i]);
         bool mg;
-        const int n = classify_lockstep<T, SQ, MOD, false>(z, F, fd.max_iter, bis, mg);
+        int n;
+        bool it1 = false;
+        if constexpr (sizeof(T) == 4) {
+            if (!fd.axis_slice) {  // the FP32 march's first-iterate form and sample position
+                it1 = true;
+                float Q0[8], Q1[8], Q2[8], dot;
+                first_iterate_coeffs<float, SQ>(F.A, D, F.c, dot, Q0, Q1, Q2);
+                first_iterate<float, 8>(vfma((float)(k_first - 1), delta, vadd(t_in, dot)), Q0, Q1, Q2, z);
+            }
+        }
+        if (it1) {
+            n = classify_lockstep_it1<T, SQ, MOD, false>(z, F, fd.max_iter, bis, mg);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) z[i] = dfma(lo, D[i], F.A[i]);
+            n = classify_lockstep<T, SQ, MOD, false>(z, F, fd.max_iter, bis, mg);
+        }
         if (bis) n_lo = n;
     }
     unsigned path = 0;

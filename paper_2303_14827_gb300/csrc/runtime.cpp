@@ -2,6 +2,7 @@
 // and scratch management of libdqj.
 #include "runtime.h"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -200,7 +201,18 @@ void axis_first_thresholds(const FrameT<float> &F, int modulus_mode, PairConsts 
         P.t_mlo = bits_f(lo);
         P.t_mhi = bits_f(above - 1);
     }
-    P.t_pad = 0.f;
+    // centre a_c and half-width margin_t of the paired kernels' band test (exact
+    // in double: every bound below is a float or the difference of two floats)
+    double need = margin;
+    float ac = INFINITY;  // empty band: |a - inf| is never within margin_t
+    if (P.t_mlo <= P.t_mhi) {
+        ac = (float)(0.5 * ((double)P.t_mlo + (double)P.t_mhi));
+        need = std::max(need, std::max((double)ac - (double)P.t_mlo, (double)P.t_mhi - (double)ac));
+    }
+    float mt = (float)need;
+    if ((double)mt < need) mt = std::nextafter(mt, INFINITY);
+    P.neg_ac = make_float2(-ac, -ac);
+    P.margin_t = mt;
 }
 
 void derive_frame(const dqj_params &p, FrameDesc &fd, int tile_w, int tile_h)
@@ -267,6 +279,7 @@ void derive_frame(const dqj_params &p, FrameDesc &fd, int tile_w, int tile_h)
     }
     fd.p2.neg1 = make_float2(-1.f, -1.f);
     fd.p2.neg2 = make_float2(-2.f, -2.f);
+    fd.p2.negR2 = make_float2(-fd.f.R2, -fd.f.R2);
     axis_first_thresholds(fd.f, p.modulus_mode, fd.p2);
     fd.W = p.width;
     fd.H = p.height;

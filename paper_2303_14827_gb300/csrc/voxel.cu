@@ -118,10 +118,11 @@ __global__ void __launch_bounds__(kBlock, 5) voxel2_kernel(const __grid_constant
             for (int i = 0; i < (AXIS ? 3 : 8); ++i)  // AXIS: components 3..7 are zero
                 z[i] = f2fma(px, make_float2(F.E[0][i], F.E[0][i]), make_float2(ba[i], bb[i]));
             int ca, cb;
-            bool mga, mgb;
+            bool live;
+            float2 dm;
             const bool va_ = aa, vb_ = ab;
-            classify_lockstep2<SQ, MOD, RECHECK, AXIS>(z, fd.p2, F.R2, F.margin, fd.max_iter, aa, ab, ca, cb, mga,
-                                                       mgb);
+            classify_lockstep2<SQ, MOD, RECHECK, AXIS>(z, fd.p2, F.R2, fd.max_iter, aa, ab, ca, cb, dm, live);
+            const bool mga = dm.x <= fd.p2.margin_t, mgb = dm.y <= fd.p2.margin_t;
             const uint32_t la = ((uint32_t)k * gu + (uint32_t)j0) * gu + (uint32_t)x, lb = la + gu;
             if (lane == 0) cl32 += (uint32_t)min(32, g - x0) * (two ? 2u : 1u);
             if (va_) {
