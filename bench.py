@@ -4,13 +4,20 @@
 Workload (one step): the five seeded 1920x1080 frames (c ~ U[-0.8,0.8]^8 with
 numpy default_rng(seed), seeds 0..4), max_iter 16, 512 march steps, 10 bisection
 steps, central-difference normals (h = 1e-4), ambient+diffuse shading to RGBA8,
-FP32 throughout.  Inputs (parameter blocks) and output planes (24 B/pixel) stay
-resident on the device; a 256 MiB buffer is written between steps to flush L2.
+in the contract-accurate mode: FP32 with an FP64 recheck of every sample whose
+escape test came within 1e-3 relative of R^2 (FP32 + FP64 recheck), the mode
+held to the parity contract on whole frames.  Inputs (parameter blocks) and
+output planes (24 B/pixel) stay resident on the device; a 256 MiB buffer is
+written between steps to flush L2.
 
 Metric: DQ iterations/s (algorithmic iterations: escape count, or max_iter for an
 inside sample, plus the n* steps of each normal evaluation, counted by the
 kernels) with frames/s beside it; roofline of the march kernel against the FP32
 FMA peak (152 SMs x 128 lanes x 2 flop x 2070 MHz), 52 flops per DQ iteration.
+Beside it: plain FP32 (outside the parity contract, with its measured
+differences from the all-FP64 render), the precision report, a general slice
+frame, the served form (10,000 Poisson requests), the 64-frame batch, the
+256x256 frame and the CPU oracle.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl dqj|reference]
 
@@ -39,7 +46,9 @@ SEEDS = (0, 1, 2, 3, 4)
 FLOPS_PER_ITER = 52          # specialised square + c + EUCLID8 modulus test, FMA = 2 flops
 SM_MAX_MHZ = 2070.0
 FP32_LANES_PER_SM = 128
-WORKLOAD = "dq-julia 1920x1080, c~U[-0.8,0.8]^8 seeds 0-4, max_iter 16, 512 march + 10 bisect, FP32"
+WORKLOAD = "dq-julia 1920x1080, c~U[-0.8,0.8]^8 seeds 0-4, max_iter 16, 512 march + 10 bisect"
+MODE_NAMES = {0: "FP32", 1: "FP32 + FP64 recheck (margin 1e-3)", 2: "FP64"}
+DTYPES = {0: "f32", 1: "f32+f64-recheck", 2: "f64"}
 KERNEL_SOURCES = ("paper_2303_14827_gb300/csrc/render.cu", "paper_2303_14827_gb300/csrc/render_common.cuh",
                   "paper_2303_14827_gb300/csrc/dq_math.cuh", "paper_2303_14827_gb300/csrc/dqj_internal.h")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "march_kernel_1080p.md")
@@ -53,15 +62,15 @@ def kernel_sha() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic():
-    """DRAM bytes per march launch from the committed ncu summary, if it was
-    taken on the current kernel sources."""
+def recorded_traffic(tag: str):
+    """DRAM bytes per march launch (`tag`: recheck, plain or general) from the
+    committed ncu summary, if it was taken on the current kernel sources."""
     try:
         text = open(TRAFFIC_FILE).read()
     except OSError:
         return None
     m = re.search(r"kernel_sha256_16:\s*([0-9a-f]+)", text)
-    t = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    t = re.search(r"traffic_bytes_per_launch\[%s\]:\s*([0-9.eE+]+)" % re.escape(tag), text)
     if not m or not t or m.group(1) != kernel_sha():
         return None
     return float(t.group(1))
@@ -253,21 +262,20 @@ def run_reference(args, world, rank):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
-def run_gpu(args, world, rank, local):
+def fp32_peak_tflops(local) -> tuple:
+    import torch
+    num_sms = torch.cuda.get_device_properties(local).multi_processor_count
+    peak = num_sms * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    return peak, f"{num_sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {SM_MAX_MHZ:.0f} MHz (max clock)"
+
+
+def timed_frames(ctx, frames, outs, steps, warmup, local, world, flush):
+    """Render `frames` once per step (W warm-up steps, then K timed steps between
+    barriers, the L2 flushed before each step).  Returns (max-over-ranks ms,
+    per-frame stats, per-launch pass times of the timed renders, clocks)."""
     import torch
 
-    from paper_2303_14827_gb300 import binding, scenes
-
-    torch.cuda.set_device(local)
-    binding.load()
-    frames = workload_scenes(args.precision)
-    nf = len(frames)
-    W, H = frames[0]["width"], frames[0]["height"]
-    ctx = binding.dqj_create(local)
-    ring = nf * (args.steps + 1)
-    binding.dqj_set_profiling(ctx, min(ring, 4096))
-    outs = [binding.alloc_outputs(W, H, device=f"cuda:{local}") for _ in frames]
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{local}")
+    from paper_2303_14827_gb300 import binding
     stream = torch.cuda.current_stream(local)
     sh = stream.cuda_stream
 
@@ -276,67 +284,128 @@ def run_gpu(args, world, rank, local):
         for s, o in zip(frames, outs):
             binding.dqj_render(ctx, s, binding.outputs_of(o), sh)
 
-    for i in range(args.warmup):
+    for i in range(warmup):
         step(i)
     torch.cuda.synchronize()
     st = [binding.stats_dict(o["stats"]) for o in outs]
-    iters_per_step = sum(x["class_iters"] + x["normal_iters"] for x in st)
-    march_iters = [x["march_iters"] for x in st]
-
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier(world)
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         e0.record(stream)
-        for i in range(args.steps):
-            step(args.warmup + i)
+        for i in range(steps):
+            step(warmup + i)
         e1.record(stream)
         torch.cuda.synchronize()
     barrier(world)
-    ms = e0.elapsed_time(e1)
-    ms_max = max_over_ranks(ms, world)
-    pass_ms = binding.dqj_pass_ms(ctx, nf * args.steps)
+    ms = max_over_ranks(e0.elapsed_time(e1), world)
+    pass_ms = binding.dqj_pass_ms(ctx, len(frames) * steps)
     st2 = [binding.stats_dict(o["stats"]) for o in outs]
-    assert st2 == st, "iteration counts changed between steps"
+    assert [x["march_iters"] for x in st2] == [x["march_iters"] for x in st], "iteration counts changed between steps"
+    return ms, st, pass_ms, clk.summary()
 
-    total_iters = iters_per_step * args.steps * world
-    value = total_iters / (ms_max * 1e-3)
-    fps = nf * args.steps * world / (ms_max * 1e-3)
 
-    # roofline of the dominant kernel (the march), over every launch of the region
+def march_roofline(pass_ms, stats, peak, peak_basis, kernel, traffic, clocks=None):
+    """Algorithmic FP32 flops of the march kernel (52 per DQ iteration it
+    performed) over its CUDA-event time, every launch of the timed region."""
+    nf = len(stats)
     march_ms = [p[0] for p in pass_ms]
-    march_flops = sum(FLOPS_PER_ITER * march_iters[i % nf] for i in range(len(march_ms)))
-    achieved = march_flops / (sum(march_ms) * 1e-3) / 1e12
-    num_sms = torch.cuda.get_device_properties(local).multi_processor_count
-    peak = num_sms * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    clocks = clk.summary()
+    flops = sum(FLOPS_PER_ITER * stats[i % nf]["march_iters"] for i in range(len(march_ms)))
+    achieved = flops / (sum(march_ms) * 1e-3) / 1e12
     roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
-            "frac": round(achieved / peak, 4), "traffic": recorded_traffic(),
-            "kernel": "march2_kernel<ALGEBRAIC,EUCLID8>", "launches": len(march_ms),
-            "avg_launch_ms": round(sum(march_ms) / len(march_ms), 4),
-            "flops_per_iter": FLOPS_PER_ITER,
-            "peak_basis": f"{num_sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {SM_MAX_MHZ:.0f} MHz (max clock)"}
-    if clocks.get("sm_mhz"):
+            "frac": round(achieved / peak, 4), "traffic": traffic, "kernel": kernel, "launches": len(march_ms),
+            "avg_launch_ms": round(sum(march_ms) / len(march_ms), 4), "flops_per_iter": FLOPS_PER_ITER,
+            "peak_basis": peak_basis}
+    if clocks and clocks.get("sm_mhz"):
         roof["frac_at_sampled_clock"] = round(achieved / (peak * clocks["sm_mhz"] / SM_MAX_MHZ), 4)
+    return roof
 
+
+def mode_section(ctx, frames, outs, steps, warmup, local, world, flush, peak, basis, kernel, tag):
+    """One precision mode on `frames`: ms per frame, DQ iterations/s, frames/s,
+    mean per-pass times and the march roofline."""
+    ms, st, pass_ms, clocks = timed_frames(ctx, frames, outs, steps, warmup, local, world, flush)
+    nf = len(frames)
+    it = sum(x["class_iters"] + x["normal_iters"] for x in st)
+    return {"ms_per_frame": round(ms / (steps * nf), 4), "iters_per_s": it * steps * world / (ms * 1e-3),
+            "frames_per_s": nf * steps * world / (ms * 1e-3),
+            "pass_ms_mean": [round(sum(p[i] for p in pass_ms) / len(pass_ms), 4) for i in range(4)],
+            "rechecks_per_frame": [x["rechecks"] for x in st], "fixups_per_frame": [x["fixups"] for x in st],
+            "roofline": march_roofline(pass_ms, st, peak, basis, kernel, recorded_traffic(tag), clocks),
+            "clocks": clocks}, ms, st, pass_ms, clocks
+
+
+def run_gpu(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_2303_14827_gb300 import binding, scenes
+
+    torch.cuda.set_device(local)
+    binding.load()
+    prec = args.precision
+    frames = workload_scenes(prec)
+    nf = len(frames)
+    W, H = frames[0]["width"], frames[0]["height"]
+    ctx = binding.dqj_create(local)
+    binding.dqj_set_profiling(ctx, min(nf * (args.steps + 1), 4096))
+    outs = [binding.alloc_outputs(W, H, device=f"cuda:{local}") for _ in frames]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{local}")
+    peak, basis = fp32_peak_tflops(local)
+    kname = {0: "march2_kernel<ALGEBRAIC,EUCLID8,plain,axis>", 1: "march2_kernel<ALGEBRAIC,EUCLID8,recheck,axis>",
+             2: "march_kernel<double,ALGEBRAIC,EUCLID8>"}
+
+    # the headline: the workload frames in the requested mode (default: FP32 + FP64 recheck)
+    ms, st, pass_ms, clocks = timed_frames(ctx, frames, outs, args.steps, args.warmup, local, world, flush)
+    iters_per_step = sum(x["class_iters"] + x["normal_iters"] for x in st)
+    value = iters_per_step * args.steps * world / (ms * 1e-3)
+    fps = nf * args.steps * world / (ms * 1e-3)
+    roof = march_roofline(pass_ms, st, peak, basis, kname[prec],
+                          recorded_traffic({0: "plain", 1: "recheck"}.get(prec, "fp64")), clocks)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == 0 else
-        ("f32+f64-recheck" if args.precision == 1 else "f64"), "data": "synthetic",
-        "config": {"workload": WORKLOAD, "frames_per_step": nf, "width": W, "height": H, "max_iter": 16,
-                   "march_steps": 512, "bisect_steps": 10, "precision": args.precision,
-                   "l2": "256 MiB buffer written between steps", "parallelism": f"replica x{world}"},
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[prec], "data": "synthetic",
+        "config": {"workload": WORKLOAD + ", " + MODE_NAMES[prec], "frames_per_step": nf, "width": W, "height": H,
+                   "max_iter": 16, "march_steps": 512, "bisect_steps": 10, "precision": prec,
+                   "recheck_margin": 1e-3, "l2": "256 MiB buffer written between steps",
+                   "parallelism": f"replica x{world}"},
         "frames_per_s": fps,
         "iters_per_frame": [x["class_iters"] + x["normal_iters"] for x in st],
         "hits_per_frame": [x["hits"] for x in st],
+        "rechecks_per_frame": [x["rechecks"] for x in st],
+        "fixups_per_frame": [x["fixups"] for x in st],
         "pass_ms_mean": [round(sum(p[i] for p in pass_ms) / len(pass_ms), 4) for i in range(4)],
+        "pass_names": ["march", "bisect+normal+shade", "fp64 recheck", "fp64 re-render"],
         "roofline": roof,
         "clocks": clocks,
-        "gpu_launches": (2 if args.precision != 1 else 4) * nf * args.steps,
+        "gpu_launches": (4 if prec == 1 else 2) * nf * args.steps,
     }
 
-    # end to end through the public API with host buffers
+    # plain FP32 beside it: faster, outside the parity contract (see its differences below)
+    if prec != 0:
+        f0 = workload_scenes(0)
+        sec, _, _, _, _ = mode_section(ctx, f0, outs, args.steps, args.warmup, local, world, flush, peak, basis,
+                                       kname[0], "plain")
+        sec["parity"] = ("outside the parity contract: escape decisions within FP32 rounding of R^2 are not "
+                         "rechecked; see precision_report for its differences from the all-FP64 render")
+        line["plain_fp32"] = sec
+
+    # a general slice frame: random orthonormal slice frame in R^8 (first-iterate form)
+    rng = np.random.default_rng(7)
+    gen = [scenes.full_hd_scene(k, precision=p, slice_basis=scenes.random_slice_frame(rng))
+           for k, p in ((0, 0), (1, 0), (2, 0))]
+    gsec = {"workload": "1920x1080, c~U[-0.8,0.8]^8 seeds 0-2, slice frame = QR of an 8x3 Gaussian "
+                        "(default_rng(7)), max_iter 16, 512 march + 10 bisect"}
+    for p, tag in ((1, "recheck"), (0, "plain")):
+        fr = [dict(g, precision=p) for g in gen]
+        sec, _, _, _, _ = mode_section(ctx, fr, outs[:3], max(3, args.steps // 3), args.warmup, local, world,
+                                       flush, peak, basis, f"march2_kernel<ALGEBRAIC,EUCLID8,{tag},general>",
+                                       "general_" + tag)
+        gsec[tag] = sec
+    line["general_slice"] = gsec
+
+    # end to end through the public API with host buffers, in the headline mode
     if not args.no_e2e:
         host = []
         for _ in frames:
@@ -359,9 +428,14 @@ def run_gpu(args, world, rank, local):
                        "h2d_bytes_per_step": nf * binding.ctypes.sizeof(binding.dqj_params),
                        "d2h_bytes_per_step": nf * (W * H * 24 + 8 * binding.DQJ_NSTATS),
                        "frames_per_s": nf * args.steps * world / dt}
+    binding.dqj_destroy(ctx)
+    del outs, flush
+    torch.cuda.empty_cache()
 
+    if not args.no_precision_report:
+        line["precision_report"] = precision_section(local)
     if not args.no_serve:
-        line["served"] = serving_section(local)
+        line["served"] = serving_section(local, n_sat=512, n_stream=args.requests, rates=(0.8, 1.0))
         line["batch64"] = batch_section(local)
 
     line["c1"] = c1_section(local)
@@ -370,7 +444,6 @@ def run_gpu(args, world, rank, local):
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
                                 "full_frames": oracle_full_frames()}
 
-    binding.dqj_destroy(ctx)
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
@@ -932,7 +1005,9 @@ def main():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("dqj", "reference"), default="dqj")
-    ap.add_argument("--precision", type=int, default=0, choices=(0, 1, 2))
+    ap.add_argument("--precision", type=int, default=1, choices=(0, 1, 2),
+                    help="headline mode: 0 FP32, 1 FP32 + FP64 recheck (default), 2 FP64")
+    ap.add_argument("--no-precision-report", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

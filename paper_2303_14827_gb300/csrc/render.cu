@@ -135,17 +135,7 @@ __global__ void __launch_bounds__(kBlock, AXIS ? 5 : 4)  // the general form kee
         if (tile >= ntiles) break;
         // counters are added per tile, so none stays live across the march loop
         LaneStats st;
-        if constexpr (AXIS) {
-            march2_tile<SQ, MOD, RECHECK, AXIS>(fd, fd.p2, sc, tile, st, stage[RECHECK ? threadIdx.x >> 5 : 0]);
-        } else {
-            // the general form takes the pair constants from a copy, as the
-            // serving kernel does: with them read from the parameter bank
-            // the first-iterate setup compiled to a result that differed
-            // from the scalar kernel's and the serving kernel's (up to two
-            // iterations per frame, no pixel changed)
-            PairConsts P = fd.p2;
-            march2_tile<SQ, MOD, RECHECK, AXIS>(fd, P, sc, tile, st, stage[RECHECK ? threadIdx.x >> 5 : 0]);
-        }
+        march2_tile<SQ, MOD, RECHECK, AXIS>(fd, fd.p2, sc, tile, st, stage[RECHECK ? threadIdx.x >> 5 : 0]);
         flush_lane_stats<false>(sc, st, true);
     }
 }
@@ -175,38 +165,10 @@ __global__ void __launch_bounds__(kBlock) bisect_kernel(const __grid_constant__ 
 template <int SQ, int MOD>
 __global__ void __launch_bounds__(kBlock) recheck_kernel(const __grid_constant__ FrameDesc fd, const Scratch sc)
 {
-    const FrameT<double> &F = fd.d;
     const unsigned total = *(volatile unsigned *)&sc.ctr->queue_count;
     const unsigned nq = min(total, sc.queue_cap);
-    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += gridDim.x * blockDim.x) {
-        const int4 e = sc.queue[i];
-        const int pixel = e.x, k = e.y & 0xffff, b = e.y >> 16;
-        const int x = pixel % fd.W, y = pixel / fd.W;
-        double d[3], t_in, t_out;
-        camera_clip<double>(F, fd.W, fd.H, x, y, d, t_in, t_out);
-        const double delta = (t_out - t_in) / (double)fd.N;
-        double t;
-        if (b == kMarchSample) {
-            t = t_in + (double)k * delta;
-        } else {
-            double lo = t_in + (double)(k - 1) * delta, hi = t_in + (double)k * delta;
-            for (int l = 0; l < b; ++l) {
-                const double mid = lo + 0.5 * (hi - lo);
-                if ((unsigned)e.z >> l & 1u)
-                    lo = mid;
-                else
-                    hi = mid;
-            }
-            t = lo + 0.5 * (hi - lo);
-        }
-        double z[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-            z[j] = F.O[j] + (F.eye[0] + t * d[0]) * F.E[0][j] + (F.eye[1] + t * d[1]) * F.E[1][j] +
-                   (F.eye[2] + t * d[2]) * F.E[2][j];
-        const int n64 = classify_scalar<double, SQ, MOD>(z, F, fd.max_iter);
-        if (n64 != e.w) mark_dirty(fd, sc, pixel);
-    }
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += gridDim.x * blockDim.x)
+        recheck_entry<SQ, MOD>(fd, sc, sc.queue[i]);
     // a full queue: pixels whose samples did not fit were flagged by the pushers
 }
 

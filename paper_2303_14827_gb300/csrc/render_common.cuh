@@ -223,11 +223,51 @@ __device__ __forceinline__ void shade_write(const FrameDesc &fd, const FrameT<T>
             make_uchar4(to_u8(v * F.albedo[0]), to_u8(v * F.albedo[1]), to_u8(v * F.albedo[2]), 255);
 }
 
-// Recheck entries of one warp are staged in shared memory and appended to the
-// frame's queue in one block per tile: a single atomic per tile instead of one
-// per round with a marginal sample, which left the warp waiting on the
-// contended queue counter.  kQStage entries per warp; a round adds at most 64.
-constexpr int kQStage = 128;
+// FP64 recheck of one queued sample {pixel, k | b << 16, path, n32}: the sample
+// is recomputed from the FP64 camera ray with the oracle's formulas (a march
+// sample t_in + k delta, or bisection level b of the bracket (k - 1, k) replayed
+// from the path bits), classified in FP64, and the pixel is queued for an FP64
+// re-render when its FP64 escape count differs from the FP32 one.
+template <int SQ, int MOD>
+__device__ __forceinline__ void recheck_entry(const FrameDesc &fd, const Scratch &sc, int4 e)
+{
+    const FrameT<double> &F = fd.d;
+    const int pixel = e.x, k = e.y & 0xffff, b = e.y >> 16;
+    const int x = pixel % fd.W, y = pixel / fd.W;
+    double d[3], t_in, t_out;
+    camera_clip<double>(F, fd.W, fd.H, x, y, d, t_in, t_out);
+    const double delta = (t_out - t_in) / (double)fd.N;
+    double t;
+    if (b == kMarchSample) {
+        t = t_in + (double)k * delta;
+    } else {
+        double lo = t_in + (double)(k - 1) * delta, hi = t_in + (double)k * delta;
+        for (int l = 0; l < b; ++l) {
+            const double mid = lo + 0.5 * (hi - lo);
+            if ((unsigned)e.z >> l & 1u)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        t = lo + 0.5 * (hi - lo);
+    }
+    double z[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+        z[j] = F.O[j] + (F.eye[0] + t * d[0]) * F.E[0][j] + (F.eye[1] + t * d[1]) * F.E[1][j] +
+               (F.eye[2] + t * d[2]) * F.E[2][j];
+    const int n64 = classify_scalar<double, SQ, MOD>(z, F, fd.max_iter);
+    if (n64 != e.w) mark_dirty(fd, sc, pixel);
+}
+
+// Recheck entries of one warp are staged in shared memory.  At the end of its
+// tile the warp rechecks them itself in FP64 (recheck_staged): that FP64 work
+// overlaps with the FP32 march of the other warps on the SM instead of running
+// as a pass of its own after the march.  A tile that fills the stage
+// (kQStage entries per warp; a round adds at most 64) appends the staged
+// entries to the frame's queue instead, in one block (one atomic), for the
+// recheck pass.
+constexpr int kQStage = 256;
 // Ray parameter of a half without a sample in the recheck march: its first
 // iterate overflows (modulus +inf) and the later ones are infinite or NaN, so
 // its distance from R^2 never falls within a recheck band.
@@ -255,6 +295,18 @@ __device__ __forceinline__ void flush_staged(const FrameDesc &fd, const Scratch 
             mark_dirty(fd, sc, e.x);
         }
     }
+    __syncwarp();
+}
+
+// FP64 recheck of a warp's staged entries qs[0, qn) (qn warp-uniform), one per
+// lane, counted as rechecks.
+template <int SQ, int MOD>
+__device__ __forceinline__ void recheck_staged(const FrameDesc &fd, const Scratch &sc, const int4 *qs, int qn)
+{
+    const int lane = threadIdx.x & 31;
+    __syncwarp();
+    if (lane == 0) atomicAdd(&sc.ctr->stats[4], (unsigned long long)qn);
+    for (int i = lane; i < qn; i += 32) recheck_entry<SQ, MOD>(fd, sc, qs[i]);
     __syncwarp();
 }
 
@@ -305,11 +357,18 @@ __device__ __forceinline__ void march2_tile(const FrameDesc &fd, const PairConst
         for (int i = 0; i < 8; ++i) D[i] = make_float2(Da[i], Db[i]);
         tin = make_float2(tia, tib);
         if constexpr (!AXIS) {
-            float2 dot, Q0[8];
-            first_iterate_coeffs<float2, SQ>(P.A, D, P.c, dot, Q0, Q1, Q2);
+            // each ray's coefficients by the scalar code of march_kernel and
+            // bisect_chunk (same operations, so the same values), then paired
+            float Qa[3][8], Qb[3][8], dota, dotb;
+            first_iterate_coeffs<float, SQ>(F.A, Da, F.c, dota, Qa[0], Qa[1], Qa[2]);
+            first_iterate_coeffs<float, SQ>(F.A, Db, F.c, dotb, Qb[0], Qb[1], Qb[2]);
 #pragma unroll
-            for (int i = 0; i < 8; ++i) D[i] = Q0[i];
-            tin = f2add(tin, dot);
+            for (int i = 0; i < 8; ++i) {
+                D[i] = make_float2(Qa[0][i], Qb[0][i]);
+                Q1[i] = make_float2(Qa[1][i], Qb[1][i]);
+                Q2[i] = make_float2(Qa[2][i], Qb[2][i]);
+            }
+            tin = make_float2(vadd(tia, dota), vadd(tib, dotb));
         }
     }
     const bool boxa = acta, boxb = actb;
@@ -365,7 +424,7 @@ __device__ __forceinline__ void march2_tile(const FrameDesc &fd, const PairConst
             more = __any_sync(kFull, acta || actb);
         }
     }
-    if (RECHECK && qn > 0) flush_staged(fd, sc, qs, qn);
+    if (RECHECK && qn > 0) recheck_staged<SQ, MOD>(fd, sc, qs, qn);
     const bool hita = kfa >= 0, hitb = kfb >= 0;
     // iterations = sum of (escape count) over escaped samples + max_iter per inside sample
     //            = sum of bounded steps + number of escaped samples
