@@ -1,12 +1,14 @@
 """Whole 1920x1080 frames against the FP64 oracle (every pixel; the oracle renders
-a frame in a few seconds on the host cores).
+a frame in a few seconds on the host cores): the five frames the benchmark
+times (seeds 0-4), the default c at 1080p (many hits) and a 1080p frame on a
+random orthonormal slice frame (the first-iterate form of the march).
 
-FP32 with the FP64 recheck is held to the full parity contract.  Plain FP32 is
-held to it except on pixels where an FP32-rounded escape test decided a sample
-whose modulus lay within rounding of R^2: such a pixel can keep its hit/miss
-class and still change its iteration count (a miss's largest escape count) or,
-when the decisive sample moves, its depth.  Those pixels are counted against a
-budget of 1e-4 of the frame; the recheck mode exists to remove them."""
+FP32 with the FP64 recheck is the mode held to the parity contract, on every
+pixel of every frame.  Plain FP32 is outside the contract: an FP32-rounded
+escape test of a sample whose modulus lay within rounding of R^2 can keep a
+pixel's hit/miss class and still change its iteration count (a miss's largest
+escape count) or, when the decisive sample moves, its depth.  Its test only
+bounds how many pixels that touches (1e-4 of the frame) and measures them."""
 import numpy as np
 import pytest
 
@@ -26,11 +28,11 @@ def rdr():
     r.close()
 
 
-FRAMES = {
-    "seed3": lambda: scenes.full_hd_scene(3),
-    "default_c": lambda: scenes.default_scene(width=1920, height=1080, max_iter=16, march_steps=512,
-                                              bisect_steps=10),
-}
+FRAMES = {f"seed{k}": (lambda k=k: scenes.full_hd_scene(k)) for k in range(5)}
+FRAMES["default_c"] = lambda: scenes.default_scene(width=1920, height=1080, max_iter=16, march_steps=512,
+                                                   bisect_steps=10)
+FRAMES["random_slice"] = lambda: scenes.full_hd_scene(
+    0, slice_basis=scenes.random_slice_frame(np.random.default_rng(7)))
 _oracle_cache = {}
 
 
@@ -54,7 +56,7 @@ def test_full_frame_recheck_meets_contract(rdr, name):
     assert st["rechecks"] > 0
 
 
-@pytest.mark.parametrize("name", sorted(FRAMES))
+@pytest.mark.parametrize("name", ["seed3", "default_c", "random_slice"])
 def test_full_frame_fp32_within_rounding_budget(rdr, name):
     g, _ = gpu_frame(rdr, name, scenes.PRECISION_FP32)
     o = oracle_frame(name)

@@ -119,9 +119,10 @@ def test_pitch_and_partial_planes(rdr):
     dict(square_mode=1, modulus_mode=1),
     dict(k_specular=0.5, shininess=16.0, light_dir=[0.3, 0.4, 1.0]),  # Eq. phong specular term
 ])
-def test_edge_cases(rdr, over):
-    s = scenes.default_scene(width=64, height=48, **over)
-    run_parity(rdr, s, str(over), flip_frac=2e-3)
+@pytest.mark.parametrize("precision", [scenes.PRECISION_FP32, scenes.PRECISION_FP32_RECHECK])
+def test_edge_cases(rdr, over, precision):
+    s = scenes.default_scene(width=64, height=48, precision=precision, **over)
+    run_parity(rdr, s, f"{over} precision {precision}")
 
 
 def test_random_slice_frames(rdr):
