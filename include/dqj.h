@@ -241,23 +241,30 @@ dqj_status dqj_submit(dqj_ctx *ctx, const dqj_params *p, const dqj_outputs *out,
  *   [2] requests run in the persistent launch   [3] requests run as plain frames
  *   [4] admission batches        [5] host nanoseconds spent admitting batches
  *   [6] requests completed       [7] scheduler loop iterations
+ *   [8] most requests admitted and unfinished at the same time
+ *   [9] requests of the persistent launch whose device execution (first work
+ *       item claimed to completion, by the device clock) overlapped that of
+ *       another request among the 256 that finished before it
  * An interface of this library (observability); the paper has no counterpart. */
-#define DQJ_NSERVE_STATS 8
+#define DQJ_NSERVE_STATS 10
 dqj_status dqj_serve_stats(dqj_ctx *ctx, int64_t *out);
 
-/* Order in which the persistent launch serves the admitted requests (requests
- * are admitted in arrival order; those that run as plain frames are
- * unaffected):
- *   DQJ_SERVE_FIFO      admission order (the default);
+/* Order in which queued requests are admitted and the persistent launch
+ * serves the admitted ones (requests that run as plain frames keep their
+ * admission position):
+ *   DQJ_SERVE_FIFO      arrival order (the default);
  *   DQJ_SERVE_SHORTEST  earliest estimated finish: each request's key is its
  *                       arrival time at dqj_submit plus an estimate of its own
  *                       march time (width x height x (march_steps + 1) samples
  *                       at 2^-9 ns each).  Small requests overtake a large one
  *                       that arrived less than their difference in cost
- *                       earlier; no request is overtaken by one that arrives
- *                       after its own estimated finish, so none starves.
- * Applies to requests admitted after the call; results are unchanged (every
- * request equals its dqj_render alone).  DQJ_ERR_INVALID for an unknown policy.
+ *                       earlier, in the host queue (admission waits for the
+ *                       memory budget and a device slot in key order) and on
+ *                       the device; no request is overtaken by one that
+ *                       arrives after its own estimated finish, so none starves.
+ * A request takes the policy in force when it is submitted; results are
+ * unchanged (every request equals its dqj_render alone).  DQJ_ERR_INVALID for
+ * an unknown policy.
  * An interface of this library (serving latency); the paper has no counterpart. */
 #define DQJ_SERVE_FIFO 0
 #define DQJ_SERVE_SHORTEST 1

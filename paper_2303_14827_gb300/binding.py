@@ -328,7 +328,8 @@ def dqj_render_voxels(ctx: int, scene: dict, grid_n: int, occupancy, outputs: dq
                                    ctypes.byref(outputs), ctypes.c_void_p(stream)))
 
 
-SERVE_STAT_NAMES = ("launches", "restarts", "packed", "plain", "batches", "admit_ns", "completed", "loops")
+SERVE_STAT_NAMES = ("launches", "restarts", "packed", "plain", "batches", "admit_ns", "completed", "loops",
+                    "max_active", "overlapped")
 
 
 DQJ_SERVE_FIFO, DQJ_SERVE_SHORTEST = 0, 1

@@ -260,6 +260,143 @@ __device__ __forceinline__ void recheck_entry(const FrameDesc &fd, const Scratch
     if (n64 != e.w) mark_dirty(fd, sc, pixel);
 }
 
+// Re-render of one pixel by one warp (all 32 lanes call), with the oracle's
+// formulas for the sample positions (the reference sequence of steps) in FP64;
+// a march sample is classified in FP32 and again in FP64 only when it is
+// marginal; bisection (five levels per round across the lanes) and normals are
+// FP64.  The lanes classify 32 consecutive march samples at a time; a ballot
+// finds the first inside one and warp reductions give the largest escape count
+// before it, so the result and the iteration count are those of the
+// sample-by-sample loop.  Bisection runs on every lane alike; the six normal
+// evaluations run on lanes 0..5.  Adds the iterations to its (per lane) and the
+// pixel to npx (lane 0).
+template <int SQ, int MOD>
+__device__ __forceinline__ void fixup_pixel(const FrameDesc &fd, int pixel, unsigned long long &its,
+                                            unsigned long long &npx)
+{
+    const FrameT<double> &F = fd.d;
+    const int lane = threadIdx.x & 31;
+    do {
+        const int x = pixel % fd.W, y = pixel / fd.W;
+        npx += lane == 0 ? 1 : 0;
+        double d[3], t_in, t_out;
+        if (!camera_clip<double>(F, fd.W, fd.H, x, y, d, t_in, t_out)) {
+            if (lane == 0) write_miss<double>(fd, x, y, 0);
+            break;
+        }
+        const double delta = (t_out - t_in) / (double)fd.N;
+        auto slice = [&](double t, double (&z)[8]) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                z[j] = F.O[j] + (F.eye[0] + t * d[0]) * F.E[0][j] + (F.eye[1] + t * d[1]) * F.E[1][j] +
+                       (F.eye[2] + t * d[2]) * F.E[2][j];
+        };
+        auto cls = [&](double t) {
+            double z[8];
+            slice(t, z);
+            return classify_scalar<double, SQ, MOD>(z, F, fd.max_iter);
+        };
+        // a march sample: FP32 first, FP64 only when some FP32 modulus came within
+        // the recheck margin of R^2 (the premise of the recheck mode: outside the
+        // margin FP32 decides as FP64 does)
+        auto cls_march = [&](double t) {
+            double z[8];
+            slice(t, z);
+            float zf[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) zf[j] = (float)z[j];
+            bool marginal;
+            const int n32 = classify_scalar_margin<float, SQ, MOD>(zf, fd.f, fd.max_iter, marginal);
+            return marginal ? classify_scalar<double, SQ, MOD>(z, F, fd.max_iter) : n32;
+        };
+        int esc_max = 0, n_prev = 0, k_first = -1;
+        for (int k0 = 0; k0 <= fd.N; k0 += 32) {
+            const int k = k0 + lane;
+            const bool part = k <= fd.N;
+            const int n = part ? cls_march(t_in + (double)k * delta) : 1;
+            const unsigned inside = __ballot_sync(kFull, part && n == 0);
+            const int first = inside ? __ffs(inside) - 1 : 32;  // samples before it escaped
+            if (part && lane <= first) its += n ? (unsigned)n : (unsigned)fd.max_iter;
+            int m = part && lane < first ? n : 0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(kFull, m, o));
+            esc_max = max(esc_max, m);
+            if (inside) {
+                if (first > 0) n_prev = __shfl_sync(kFull, n, first - 1);  // else: last of the previous chunk
+                k_first = k0 + first;
+                break;
+            }
+            n_prev = __shfl_sync(kFull, n, 31);
+        }
+        if (k_first < 0) {
+            if (lane == 0) write_miss<double>(fd, x, y, esc_max);
+            break;
+        }
+        double depth = t_in;
+        int n_star = fd.max_iter;
+        if (k_first > 0) {
+            double lo = t_in + (double)(k_first - 1) * delta, hi = t_in + (double)k_first * delta;
+            n_star = n_prev;
+            // Bisection, up to five levels per round: lane j - 1 holds node j of the
+            // level tree (node 1 the next midpoint, children 2j: inside -> [lo, mid],
+            // 2j + 1: outside -> [mid, hi]), derives its interval with the same
+            // operations as the sequential halvings and classifies its midpoint;
+            // the path is then replayed, so the bracket is the sequential one.
+            for (int b0 = 0; b0 < fd.B; b0 += 5) {
+                const int levels = min(5, fd.B - b0);
+                const int node = lane + 1;
+                const int depth_j = 31 - __clz(node);  // level of the node
+                int n = 1;
+                if (depth_j < levels) {
+                    double l = lo, h = hi;
+                    for (int q = depth_j - 1; q >= 0; --q) {  // path bits below the leading one
+                        const double mid = l + 0.5 * (h - l);
+                        if ((node >> q) & 1)
+                            l = mid;
+                        else
+                            h = mid;
+                    }
+                    n = cls(l + 0.5 * (h - l));
+                }
+                int cur = 1;
+                for (int q = 0; q < levels; ++q) {
+                    const int nq = __shfl_sync(kFull, n, cur - 1);
+                    const double mid = lo + 0.5 * (hi - lo);
+                    if (lane == 0) its += nq ? (unsigned)nq : (unsigned)fd.max_iter;
+                    if (nq == 0) {
+                        hi = mid;
+                        cur = 2 * cur;
+                    } else {
+                        lo = mid;
+                        n_star = nq;
+                        cur = 2 * cur + 1;
+                    }
+                }
+            }
+            depth = lo + 0.5 * (hi - lo);
+        }
+        // normal: lane 2a + s evaluates F at p +- h e_a
+        double fv = 0.0;
+        if (lane < 6) {
+            const int a = lane >> 1;
+            double p[3] = {F.eye[0] + depth * d[0], F.eye[1] + depth * d[1], F.eye[2] + depth * d[2]};
+            p[a] += (lane & 1) == 0 ? F.h : -F.h;
+            double z[8];
+            for (int j = 0; j < 8; ++j) z[j] = F.O[j] + p[0] * F.E[0][j] + p[1] * F.E[1][j] + p[2] * F.E[2][j];
+            double sp = dq_sp<double>(z);
+            for (int n = 0; n < n_star; ++n) dq_iter<double, SQ, MOD>(z, z, sp, F.c);
+            its += (unsigned)n_star;
+            fv = modulus<double, MOD>(z);
+        }
+        const bool bad = lane < 6 && !(fv <= normal_fmax(0.0));
+        const bool guard = __any_sync(kFull, bad);
+        double g[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) g[a] = __shfl_sync(kFull, fv, 2 * a) - __shfl_sync(kFull, fv, 2 * a + 1);
+        if (lane == 0) shade_write<double>(fd, F, x, y, n_star, depth, g, guard, d);
+    } while (false);
+}
+
 // Recheck entries of one warp are staged in shared memory.  At the end of its
 // tile the warp rechecks them itself in FP64 (recheck_staged): that FP64 work
 // overlaps with the FP32 march of the other warps on the SM instead of running

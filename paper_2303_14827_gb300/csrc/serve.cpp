@@ -2,12 +2,16 @@
 // dqj_destroy and the scheduler thread behind them (continuous batching).
 //
 // A request is queued on the host at dqj_submit.  The scheduler thread admits
-// queued requests in arrival order while the sum of the admitted requests'
-// footprints (output planes + scratch + slot) fits the context's memory budget
-// and a device slot is free.  Admitted FP32 / algebraic / EUCLID8 requests are
+// queued requests in the order of the serving policy (arrival, or earliest
+// estimated finish) while the sum of the admitted requests' footprints (output
+// planes + scratch + slot) fits the context's memory budget and a device slot
+// is free.  dqj_poll reads ticket states under a lock of their own, never the
+// scheduler's.  Admitted FP32 / algebraic / EUCLID8 requests are
 // written into device slots and run together in one persistent launch
-// (serve.cu); requests arriving while it runs join it.  Other precisions and
-// modes run as ordinary stream-ordered frames on the serving stream.  Completed
+// (serve.cu); requests arriving while it runs join it.  FP32 + FP64 recheck
+// requests run in it too, with their recheck and re-render phases.  Other
+// precisions and modes run as ordinary stream-ordered frames on the serving
+// stream.  Completed
 // requests release their budget, and dqj_poll hands back their status once.
 //
 // The scheduler talks to the device through a small backend interface.  The
@@ -18,6 +22,7 @@
 #include <algorithm>
 #include <chrono>
 #include <deque>
+#include <unordered_map>
 #include <cstdlib>
 #include <cstring>
 #include <memory>
@@ -60,15 +65,19 @@ struct Request {
 
 bool packable(const dqj_params &p)
 {
-    return p.precision == DQJ_FP32 && p.square_mode == DQJ_SQUARE_ALGEBRAIC && p.modulus_mode == DQJ_MODULUS_EUCLID8 &&
-           p.traversal == DQJ_TRAVERSAL_MARCH;
+    return (p.precision == DQJ_FP32 || p.precision == DQJ_FP32_RECHECK) && p.square_mode == DQJ_SQUARE_ALGEBRAIC &&
+           p.modulus_mode == DQJ_MODULUS_EUCLID8 && p.traversal == DQJ_TRAVERSAL_MARCH;
 }
+
+// Recheck scratch per pixel: queue (4 entries), per-pixel tag, re-render list.
+constexpr uint64_t kRecheckBytesPerPixel = 4 * sizeof(int4) + 8;
 
 uint64_t scratch_bytes(const dqj_params &p, bool packed)
 {
     const uint64_t px = (uint64_t)p.width * (uint64_t)p.height;
     uint64_t b = 256 + px * sizeof(int4);                                  // counters + hit list
-    if (!packed && p.precision == DQJ_FP32_RECHECK) b += px * (4 * sizeof(int4) + 8);  // queue, tags, list
+    if (p.precision == DQJ_FP32_RECHECK) b += px * kRecheckBytesPerPixel;   // queue, tags, list
+    (void)packed;
     return b;
 }
 
@@ -100,6 +109,9 @@ struct Backend {
         launches = 0;
         restarts = 0;
     }
+    // Requests in the persistent launch whose device execution (first item
+    // claimed to completion) overlapped another request's.
+    virtual int64_t overlapped() const { return 0; }
 };
 
 class GpuBackend : public Backend {
@@ -119,6 +131,11 @@ class GpuBackend : public Backend {
             std::memset(h_flags_, 0, sizeof(unsigned) * (kMaxSlots + 2));
             h_flags_[kMaxSlots] = 1;  // source of the host's exit request
             e = cudaHostGetDevicePointer(reinterpret_cast<void **>(&d_flags_), h_flags_, 0);
+        }
+        if (e == cudaSuccess) e = cudaHostAlloc(&h_times_, sizeof(unsigned long long) * 2 * kMaxSlots, cudaHostAllocMapped);
+        if (e == cudaSuccess) {
+            std::memset(h_times_, 0, sizeof(unsigned long long) * 2 * kMaxSlots);
+            e = cudaHostGetDevicePointer(reinterpret_cast<void **>(&d_times_), h_times_, 0);
         }
         if (e == cudaSuccess) e = cudaHostAlloc(&h_slots_, sizeof(ServeSlot) * kMaxSlots, cudaHostAllocDefault);
         if (e == cudaSuccess) e = cudaHostAlloc(&h_blocks_, sizeof(ReqBlock) * kReqBlocks, cudaHostAllocDefault);
@@ -265,19 +282,48 @@ class GpuBackend : public Backend {
         return DQJ_OK;
     }
 
-    // Stage a packed request's control block in host memory.
+    // Stage a packed request's control block in host memory.  Each slot owns a
+    // grow-only scratch buffer laid out by its pixel capacity: the hit list,
+    // then (recheck mode) the recheck queue, the per-pixel tags and the
+    // re-render list.  The tags of a new buffer start at zero and those of
+    // later requests in the slot are told apart by their generation (the
+    // frame's epoch).  The zeros come by a copy-engine copy from page-locked
+    // host memory: a memset may run as a kernel, which could not start while
+    // the persistent grid holds every SM.
     dqj_status stage_packed(Request &r)
     {
         const uint64_t px = (uint64_t)r.p.width * (uint64_t)r.p.height;
-        const uint64_t need = px * sizeof(int4);
+        const bool rq = r.p.precision == DQJ_FP32_RECHECK;
         cudaError_t e = cudaSuccess;
-        if (slot_cap_[r.slot] < need) {  // grow-only hit list per slot
+        if (slot_px_[r.slot] < px || (rq && !slot_rq_[r.slot])) {
+            const uint64_t cap = std::max<uint64_t>(px, slot_px_[r.slot]);
+            const bool with_rq = rq || slot_rq_[r.slot];
             if (slot_scratch_[r.slot]) e = cudaFreeAsync(slot_scratch_[r.slot], cstream_);
             slot_scratch_[r.slot] = nullptr;
-            slot_cap_[r.slot] = 0;
-            if (e == cudaSuccess) e = cudaMallocAsync(&slot_scratch_[r.slot], need, cstream_);
-            if (e != cudaSuccess) return cuda_fail(e, "serve: slot hit list");
-            slot_cap_[r.slot] = need;
+            slot_px_[r.slot] = 0;
+            slot_rq_[r.slot] = false;
+            const size_t bytes = cap * (sizeof(int4) + (with_rq ? kRecheckBytesPerPixel : 0));
+            if (e == cudaSuccess) e = cudaMallocAsync(&slot_scratch_[r.slot], bytes, cstream_);
+            if (e == cudaSuccess && with_rq) {
+                const size_t tag_bytes = cap * sizeof(uint32_t);
+                if (zeros_bytes_ < tag_bytes) {  // grow-only zero source; the stream is idle here
+                    e = cudaStreamSynchronize(cstream_);
+                    if (e == cudaSuccess && zeros_) e = cudaFreeHost(zeros_);
+                    zeros_ = nullptr;
+                    zeros_bytes_ = 0;
+                    if (e == cudaSuccess) e = cudaHostAlloc(&zeros_, tag_bytes, cudaHostAllocDefault);
+                    if (e == cudaSuccess) {
+                        std::memset(zeros_, 0, tag_bytes);
+                        zeros_bytes_ = tag_bytes;
+                    }
+                }
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(static_cast<char *>(slot_scratch_[r.slot]) + cap * 5 * sizeof(int4), zeros_,
+                                        tag_bytes, cudaMemcpyHostToDevice, cstream_);
+            }
+            if (e != cudaSuccess) return cuda_fail(e, "serve: slot scratch");
+            slot_px_[r.slot] = cap;
+            slot_rq_[r.slot] = with_rq;
         }
         unsigned bi = 0;
         dqj_status s = take_block(bi);
@@ -287,12 +333,23 @@ class GpuBackend : public Backend {
         std::memset(&h, 0, sizeof h);
         h.phase = kPhaseMarch;
         h.fd = frame_of(r);
+        h.fd.epoch = (uint32_t)r.seq;  // non-zero, unique per admission
         h.ntiles = (unsigned)h.fd.tiles_x * (unsigned)h.fd.tiles_y;
         h.slot = (unsigned)r.slot;
         h.gen = (unsigned)r.seq;
+        h.recheck = rq ? 1u : 0u;
+        char *base = static_cast<char *>(slot_scratch_[r.slot]);
+        const uint64_t cap = slot_px_[r.slot];
         h.sc.ctr = &d_blocks_[bi].ctr;
-        h.sc.hits = static_cast<int4 *>(slot_scratch_[r.slot]);
+        h.sc.hits = reinterpret_cast<int4 *>(base);
         h.sc.hit_cap = (uint32_t)px;
+        if (rq) {
+            h.sc.queue = reinterpret_cast<int4 *>(base + cap * sizeof(int4));
+            h.sc.queue_cap = (uint32_t)(4 * cap);
+            h.sc.dirty_flag = reinterpret_cast<uint32_t *>(base + cap * 5 * sizeof(int4));
+            h.sc.dirty_list = reinterpret_cast<int32_t *>(base + cap * (5 * sizeof(int4) + 4));
+            h.sc.dirty_cap = (uint32_t)px;
+        }
         return DQJ_OK;
     }
 
@@ -334,7 +391,10 @@ class GpuBackend : public Backend {
     {
         if (r.packed) {
             const unsigned v = *reinterpret_cast<volatile unsigned *>(&h_flags_[r.slot]);
-            if (v == (unsigned)r.seq) return 1;
+            if (v == (unsigned)r.seq) {
+                record_interval(r.slot);
+                return 1;
+            }
             if (launched_) {
                 const cudaError_t e = cudaEventQuery(kevent_);
                 if (e != cudaSuccess && e != cudaErrorNotReady) {
@@ -361,7 +421,7 @@ class GpuBackend : public Backend {
             completed_ = launches_;
         }
         cudaError_t e = cudaSetDevice(ctx_->device);
-        ServeCtl ctl{d_slots_, d_blocks_, d_flags_, d_exit_, d_flags_ + kMaxSlots + 1, idle_ns_, 1000000000ull};
+        ServeCtl ctl{d_slots_, d_blocks_, d_flags_, d_exit_, d_flags_ + kMaxSlots + 1, d_times_, idle_ns_, 1000000000ull};
         if (e == cudaSuccess) e = cudaMemsetAsync(d_exit_, 0, sizeof(unsigned), kstream_);  // ordered before the launch
         if (e == cudaSuccess) e = serve_launch(ctl, ctx_->num_sms, kstream_);
         if (e == cudaSuccess) e = cudaEventRecord(kevent_, kstream_);
@@ -403,7 +463,27 @@ class GpuBackend : public Backend {
         restarts = (int64_t)restarts_;
     }
 
+    int64_t overlapped() const override { return overlapped_; }
+
   private:
+    // The device interval of a finished request (written by the kernel to
+    // mapped memory before the completion flag), checked against the last
+    // kIntervals finished requests: an overlap means both ran on the device at
+    // the same time.
+    static constexpr int kIntervals = 256;
+    void record_interval(int slot)
+    {
+        volatile unsigned long long *t = h_times_ + 2 * slot;
+        const unsigned long long a = t[0], b = t[1];
+        bool over = false;
+        for (int i = 0; i < n_iv_; ++i) over = over || (a < iv_[i][1] && iv_[i][0] < b);
+        if (over) ++overlapped_;
+        iv_[iv_next_][0] = a;
+        iv_[iv_next_][1] = b;
+        iv_next_ = (iv_next_ + 1) % kIntervals;
+        n_iv_ = std::min(n_iv_ + 1, kIntervals);
+    }
+
     void free_all()
     {
         cudaSetDevice(ctx_->device);
@@ -413,6 +493,8 @@ class GpuBackend : public Backend {
         if (d_blocks_) cudaFree(d_blocks_);
         if (d_exit_) cudaFree(d_exit_);
         if (h_flags_) cudaFreeHost(h_flags_);
+        if (h_times_) cudaFreeHost(h_times_);
+        if (zeros_) cudaFreeHost(zeros_);
         if (h_slots_) cudaFreeHost(h_slots_);
         if (h_blocks_) cudaFreeHost(h_blocks_);
         if (kevent_) cudaEventDestroy(kevent_);
@@ -427,7 +509,14 @@ class GpuBackend : public Backend {
     std::deque<std::pair<unsigned, uint64_t>> free_blocks_;  // (block, launch id when retired), oldest first
     unsigned slot_block_[kMaxSlots] = {};
     void *slot_scratch_[kMaxSlots] = {};
-    uint64_t slot_cap_[kMaxSlots] = {};
+    uint64_t slot_px_[kMaxSlots] = {};  // pixel capacity of the slot's scratch
+    bool slot_rq_[kMaxSlots] = {};      // ... and whether it holds the recheck regions
+    unsigned long long *h_times_ = nullptr, *d_times_ = nullptr;  // per slot {first item, finished}
+    void *zeros_ = nullptr;  // page-locked zeros for new tag regions
+    size_t zeros_bytes_ = 0;
+    unsigned long long iv_[kIntervals][2] = {};
+    int n_iv_ = 0, iv_next_ = 0;
+    int64_t overlapped_ = 0;
     unsigned *h_flags_ = nullptr, *d_flags_ = nullptr;  // [0, kMaxSlots) done flags, [kMaxSlots] = 1, then hold
     unsigned *d_exit_ = nullptr;
     cudaStream_t kstream_ = nullptr, cstream_ = nullptr, pstream_ = nullptr;
@@ -510,9 +599,21 @@ struct ServeState {
     std::unique_ptr<Backend> backend;
     std::mutex mu;
     std::condition_variable cv;
-    std::deque<std::unique_ptr<Request>> pending;
+    // Queued requests in admission order: by (key, ticket), the key being the
+    // ticket under DQJ_SERVE_FIFO and the estimated finish (shortest_key) under
+    // DQJ_SERVE_SHORTEST, as set at dqj_submit.
+    std::map<std::pair<uint64_t, dqj_ticket>, std::unique_ptr<Request>> pending;
     std::map<dqj_ticket, std::unique_ptr<Request>> active;  // admitted, not finished
-    std::map<dqj_ticket, dqj_status> finished;              // awaiting dqj_poll
+    // Ticket states for dqj_poll, under their own lock (tmu): a client polling
+    // in a tight loop never contends for the scheduler's lock (mu), whose
+    // unfair hand-over could otherwise starve the scheduler thread.  Lock
+    // order: mu before tmu.
+    struct TicketState {
+        bool done = false;
+        dqj_status status = DQJ_OK;
+    };
+    std::mutex tmu;
+    std::unordered_map<dqj_ticket, TicketState> tickets;
     Request *slot_req[kMaxSlots] = {};
     uint64_t used = 0;
     dqj_ticket next_ticket = 1;
@@ -521,14 +622,22 @@ struct ServeState {
     std::atomic<bool> failed{false};  // the scheduler thread stopped on a host exception
     const clk::time_point t0 = clk::now();
     std::thread thr;
-    int64_t n_packed = 0, n_plain = 0, n_batches = 0, admit_ns = 0, n_completed = 0, n_loops = 0;
+    int64_t n_packed = 0, n_plain = 0, n_batches = 0, admit_ns = 0, n_completed = 0, n_loops = 0, max_active = 0;
+
+    void set_done(dqj_ticket t, dqj_status st)
+    {
+        std::lock_guard<std::mutex> lk(tmu);
+        TicketState &ts = tickets[t];
+        ts.done = true;
+        ts.status = st;
+    }
 
     void complete(Request *r, dqj_status st)
     {
         backend->release(*r);
         if (r->slot >= 0) slot_req[r->slot] = nullptr;
         used -= r->footprint;
-        finished[r->ticket] = st;
+        set_done(r->ticket, st);
         ++n_completed;
     }
 
@@ -541,7 +650,7 @@ struct ServeState {
         failed = true;
         try {
             std::lock_guard<std::mutex> lk(mu);
-            for (auto &r : pending) finished[r->ticket] = DQJ_ERR_NOMEM;
+            for (auto &kv : pending) set_done(kv.first.second, DQJ_ERR_NOMEM);
             pending.clear();
             cv.notify_all();
         } catch (...) {
@@ -566,11 +675,11 @@ struct ServeState {
                     ++it;
                 }
             }
-            // choose admissions in arrival order while the budget and a slot allow;
+            // choose admissions in queue order while the budget and a slot allow;
             // they count as active (dqj_poll sees them) while being written
             batch.clear();
             while (!draining && !pending.empty()) {
-                Request *r = pending.front().get();
+                Request *r = pending.begin()->second.get();
                 if (used + r->footprint > ctx->cfg.mem_budget_bytes) break;
                 int slot = -1;
                 if (r->packed) {
@@ -581,10 +690,11 @@ struct ServeState {
                 }
                 r->slot = slot;
                 used += r->footprint;
-                active.emplace(r->ticket, std::move(pending.front()));
-                pending.pop_front();
+                active.emplace(r->ticket, std::move(pending.begin()->second));
+                pending.erase(pending.begin());
                 batch.push_back(r);
             }
+            max_active = std::max<int64_t>(max_active, (int64_t)active.size());
             backend->hold(!pending.empty() || !active.empty());
             if (!batch.empty()) {
                 const int policy = ctx->serve_policy.load(std::memory_order_relaxed);
@@ -685,9 +795,16 @@ dqj_status dqj_submit(dqj_ctx *ctx, const dqj_params *p, const dqj_outputs *out,
         if (S.failed) return fail(DQJ_ERR_NOMEM, "serving stopped after a host allocation failure");
         if ((int64_t)S.pending.size() >= ctx->cfg.max_pending) return fail(DQJ_ERR_BUSY, "serving queue is full");
         r->ticket = S.next_ticket++;
-        *ticket = r->ticket;
         r->submitted = clk::now();
-        S.pending.push_back(std::move(r));
+        const uint64_t key = ctx->serve_policy.load(std::memory_order_relaxed) == DQJ_SERVE_SHORTEST
+                                 ? shortest_key(*r, S.t0)
+                                 : r->ticket;
+        {
+            std::lock_guard<std::mutex> tl(S.tmu);
+            S.tickets.emplace(r->ticket, ServeState::TicketState{});
+        }
+        *ticket = r->ticket;
+        S.pending.emplace(std::make_pair(key, r->ticket), std::move(r));
         S.cv.notify_all();
         return DQJ_OK;
     });
@@ -719,6 +836,8 @@ dqj_status dqj_serve_stats(dqj_ctx *ctx, int64_t *out)
         out[5] = S.admit_ns;
         out[6] = S.n_completed;
         out[7] = S.n_loops;
+        out[8] = S.max_active;
+        out[9] = S.backend->overlapped();
         return DQJ_OK;
     });
 }
@@ -729,24 +848,15 @@ dqj_status dqj_poll(dqj_ctx *ctx, dqj_ticket ticket, int *done, dqj_status *resu
         if (!ctx || !done || !result) return fail(DQJ_ERR_INVALID, "ctx, done or result is NULL");
         if (!ctx->serve) return fail(DQJ_ERR_NOT_FOUND, "unknown ticket");
         ServeState &S = *ctx->serve;
-        std::lock_guard<std::mutex> lk(S.mu);
-        auto f = S.finished.find(ticket);
-        if (f != S.finished.end()) {
-            *done = 1;
-            *result = f->second;
-            S.finished.erase(f);
-            return DQJ_OK;
+        std::lock_guard<std::mutex> lk(S.tmu);
+        auto f = S.tickets.find(ticket);
+        if (f == S.tickets.end()) return fail(DQJ_ERR_NOT_FOUND, "unknown or already consumed ticket");
+        *done = f->second.done ? 1 : 0;
+        if (f->second.done) {
+            *result = f->second.status;
+            S.tickets.erase(f);
         }
-        if (S.active.count(ticket)) {
-            *done = 0;
-            return DQJ_OK;
-        }
-        for (auto &r : S.pending)
-            if (r->ticket == ticket) {
-                *done = 0;
-                return DQJ_OK;
-            }
-        return fail(DQJ_ERR_NOT_FOUND, "unknown or already consumed ticket");
+        return DQJ_OK;
     });
 }
 
@@ -762,7 +872,7 @@ dqj_status dqj_destroy(dqj_ctx *ctx)
             {
                 std::unique_lock<std::mutex> lk(S.mu);
                 S.draining = true;
-                for (auto &r : S.pending) S.finished[r->ticket] = DQJ_ERR_CANCELLED;
+                for (auto &kv : S.pending) S.set_done(kv.first.second, DQJ_ERR_CANCELLED);
                 S.pending.clear();
                 S.cv.notify_all();
                 S.cv.wait_for(lk, std::chrono::milliseconds(timeout_ms), [&] { return S.active.empty(); });

@@ -7,15 +7,19 @@
 // request with the smallest priority key that still has unclaimed work (the
 // host sets the key: admission order, or arrival time plus the request's
 // estimated cost), claims one work item from it with an atomic add and runs it:
-//   MARCH phase : one 64-ray tile of the paired march (march2_tile);
-//   BISECT phase: 32 hit-list entries (bisect_chunk).
-// The warp that completes a request's last march tile switches it to the
-// bisection phase (or finishes it when it has no hits).  The warp that completes
-// its last bisection chunk copies the request's counters to the caller's stats
-// array and writes the request's generation to the slot's completion flag in
-// mapped host memory.  A request's results are those of dqj_render: every
-// pixel's arithmetic is independent of which warp, tile order or neighbouring
-// requests ran it.
+//   MARCH phase  : one 64-ray tile of the paired march (march2_tile; in the
+//                  recheck mode with the FP64 recheck of its staged samples);
+//   BISECT phase : 32 hit-list entries (bisect_chunk);
+//   RECHECK phase: 32 recheck-queue entries (recheck_entry), recheck mode only;
+//   FIXUP phase  : one pixel to re-render in FP64 (fixup_pixel), recheck mode.
+// The warp that completes a phase's last item moves the request to the next
+// phase that has work.  The warp that completes its last item copies the
+// request's counters to the caller's stats array and writes the request's
+// generation to the slot's completion flag in mapped host memory (the time of
+// its first claimed item and of its completion beside it).  A request's
+// results are those of dqj_render: every pixel's arithmetic is independent of
+// which warp, tile order or neighbouring requests ran it, and the passes run
+// in the same order.
 //
 // Apart from its counters a control block is immutable while published, and the
 // host reuses one only after every warp of any launch that could have seen it
@@ -34,6 +38,7 @@
 // copy-engine write) to stop the launch.
 #include "render_common.cuh"
 #include "serve_internal.h"
+#include "../../include/dqj.h"
 
 namespace dqj {
 
@@ -70,10 +75,53 @@ __device__ __forceinline__ void finish_request(ReqBlock *b, const ServeCtl &ctl,
     if (stats) {
         for (int i = 0; i < DQJ_NSTATS_DEV; ++i) stats[i] = (int64_t)ld_vol64(&b->ctr.stats[i]);
     }
+    const unsigned slot = __ldcg(&b->slot);
+    *reinterpret_cast<volatile unsigned long long *>(&ctl.times[2 * slot + 1]) = globaltimer_ns();
     __threadfence_system();
     st_release(&b->phase, kPhaseDone);
-    *reinterpret_cast<volatile unsigned *>(&ctl.done_flags[__ldcg(&b->slot)]) = __ldcg(&b->gen);
+    *reinterpret_cast<volatile unsigned *>(&ctl.done_flags[slot]) = __ldcg(&b->gen);
     __threadfence_system();
+}
+
+// Move a request whose phase `from` has completed to the next phase with work,
+// or finish it (one lane).  The counts of the next phases are final here: every
+// warp that added to them did so before it counted its item as done.
+__device__ __forceinline__ void next_phase(ReqBlock *b, const ServeCtl &ctl, const FrameDesc &fd, unsigned from)
+{
+    if (from == kPhaseMarch) {
+        const unsigned nh = min(ld_vol32(&b->ctr.hit_count), __ldcg(&b->sc.hit_cap));
+        *reinterpret_cast<volatile unsigned *>(&b->hit_total) = nh;
+        if (nh > 0) {
+            __threadfence();
+            st_release(&b->phase, kPhaseBisect);
+            return;
+        }
+        from = kPhaseBisect;
+    }
+    if (from == kPhaseBisect) {
+        if (!__ldcg(&b->recheck)) {
+            finish_request(b, ctl, fd.stats);
+            return;
+        }
+        const unsigned nq = min(ld_vol32(&b->ctr.queue_count), __ldcg(&b->sc.queue_cap));
+        *reinterpret_cast<volatile unsigned *>(&b->q_total) = nq;
+        if (nq > 0) {
+            __threadfence();
+            st_release(&b->phase, kPhaseRecheck);
+            return;
+        }
+        from = kPhaseRecheck;
+    }
+    if (from == kPhaseRecheck) {
+        const unsigned nd = min(ld_vol32(&b->ctr.dirty_count), __ldcg(&b->sc.dirty_cap));
+        *reinterpret_cast<volatile unsigned *>(&b->f_total) = nd;
+        if (nd > 0) {
+            __threadfence();
+            st_release(&b->phase, kPhaseFixup);
+            return;
+        }
+    }
+    finish_request(b, ctl, fd.stats);
 }
 
 // Has the request in block b unclaimed work?  (A hint: the claim re-checks.)
@@ -82,6 +130,8 @@ __device__ __forceinline__ bool has_work(const ReqBlock *b)
     const unsigned ph = ld_vol32(&b->phase);
     if (ph == kPhaseMarch) return ld_vol64(&b->tile_claim) < (unsigned long long)__ldcg(&b->ntiles);
     if (ph == kPhaseBisect) return ld_vol64(&b->hit_claim) < (unsigned long long)ld_vol32(&b->hit_total);
+    if (ph == kPhaseRecheck) return ld_vol64(&b->q_claim) < (unsigned long long)ld_vol32(&b->q_total);
+    if (ph == kPhaseFixup) return ld_vol64(&b->f_claim) < (unsigned long long)ld_vol32(&b->f_total);
     return false;
 }
 
@@ -99,9 +149,66 @@ __device__ __forceinline__ Scratch load_scratch(const Scratch *src)
 
 }  // namespace
 
+// The work items.  The general-slice march (first-iterate form, ~120
+// registers) and the other phases run behind calls of their own: inlined
+// into one loop with the scheduler and the axis march they spilled
+// registers in the hot loop.  The axis march, the served form's common case,
+// stays inline.
+template <bool RECHECK, bool AXIS>
+__device__ __noinline__ void march_item_general(const FrameDesc &fd, const Scratch &sc, unsigned tile, int4 *stage)
+{
+    LaneStats st;
+    march2_tile<0, 0, RECHECK, AXIS>(fd, fd.p2, sc, tile, st, stage);
+    flush_lane_stats<false>(sc, st, true);
+}
+
+template <bool RECHECK, bool AXIS>
+__device__ __forceinline__ void march_item(const FrameDesc &fd, const Scratch &sc, unsigned tile, int4 *stage)
+{
+    if constexpr (AXIS) {
+        LaneStats st;
+        march2_tile<0, 0, RECHECK, true>(fd, fd.p2, sc, tile, st, stage);
+        flush_lane_stats<false>(sc, st, true);
+    } else {
+        march_item_general<RECHECK, false>(fd, sc, tile, stage);
+    }
+}
+
+template <bool RECHECK>
+__device__ __noinline__ void bisect_item(const FrameDesc &fd, const Scratch &sc, unsigned base, unsigned nh)
+{
+    LaneStats st;
+    bisect_chunk<float, 0, 0, RECHECK>(fd, sc, base, nh, st);
+    flush_lane_stats<RECHECK>(sc, st, false);
+}
+
+__device__ __noinline__ void recheck_item(const FrameDesc &fd, const Scratch &sc, unsigned base, unsigned nq)
+{
+    const int lane = threadIdx.x & 31;
+    if (base + lane < nq) recheck_entry<0, 0>(fd, sc, __ldcg(sc.queue + base + lane));
+}
+
+__device__ __noinline__ void fixup_item(const FrameDesc &fd, const Scratch &sc, unsigned i)
+{
+    unsigned long long its = 0, npx = 0;
+    fixup_pixel<0, 0>(fd, __ldcg(sc.dirty_list + i), its, npx);
+    flush_stat(&sc.ctr->stats[6], its);
+    flush_stat(&sc.ctr->stats[5], npx);
+}
+
+// Claim up to `step` items of a phase (lane 0): the first claimed index, or
+// ~0u when the phase has none left.
+__device__ __forceinline__ unsigned claim(unsigned long long *ctr, unsigned total, unsigned step)
+{
+    if (ld_vol64(ctr) >= total) return ~0u;
+    const unsigned long long c = atomicAdd(ctr, (unsigned long long)step);
+    return c < total ? (unsigned)c : ~0u;
+}
+
 __global__ void __launch_bounds__(kBlock, 4) serve_kernel(ServeCtl ctl)
 {
     __shared__ FrameDesc s_fd[kBlock / 32];
+    __shared__ int4 s_stage[kBlock / 32][kQStage];  // recheck entries of a march tile, per warp
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     FrameDesc &fd = s_fd[wib];
@@ -135,31 +242,27 @@ __global__ void __launch_bounds__(kBlock, 4) serve_kernel(ServeCtl ctl)
         }
         // ---- claim one work item (lane 0)
         ReqBlock *b = best_block >= 0 ? &ctl.blocks[best_block] : nullptr;
-        unsigned item = 0;
-        int kind = 0;  // 1 march tile, 2 bisection chunk
+        unsigned item = ~0u, ph = kPhaseDone;
         if (b && lane == 0) {
-            const unsigned ph = ld_acquire(&b->phase);
+            ph = ld_acquire(&b->phase);  // a phase's total was written before the phase was released
             if (ph == kPhaseMarch) {
-                const unsigned long long c = atomicAdd(&b->tile_claim, 1ull);
-                if (c < (unsigned long long)__ldcg(&b->ntiles)) {
-                    item = (unsigned)c;
-                    kind = 1;
+                item = claim(&b->tile_claim, __ldcg(&b->ntiles), 1);
+                if (item == 0) {  // the request's first item: its start on the device
+                    *reinterpret_cast<volatile unsigned long long *>(&ctl.times[2 * __ldcg(&b->slot)]) =
+                        globaltimer_ns();
+                    __threadfence_system();  // visible to the host before the request's completion
                 }
             } else if (ph == kPhaseBisect) {
-                // hit_total was written before the phase was released
-                const unsigned nh = ld_vol32(&b->hit_total);
-                if (ld_vol64(&b->hit_claim) < nh) {
-                    const unsigned long long c = atomicAdd(&b->hit_claim, 32ull);
-                    if (c < nh) {
-                        item = (unsigned)c;
-                        kind = 2;
-                    }
-                }
+                item = claim(&b->hit_claim, ld_vol32(&b->hit_total), 32);
+            } else if (ph == kPhaseRecheck) {
+                item = claim(&b->q_claim, ld_vol32(&b->q_total), 32);
+            } else if (ph == kPhaseFixup) {
+                item = claim(&b->f_claim, ld_vol32(&b->f_total), 1);
             }
         }
-        kind = __shfl_sync(kFull, kind, 0);
         item = __shfl_sync(kFull, item, 0);
-        if (kind == 0) {
+        ph = __shfl_sync(kFull, ph, 0);
+        if (item == ~0u) {
             int quit = 0;
             if (lane == 0) {  // one clock reading per warp keeps the decision uniform
                 const unsigned long long now = globaltimer_ns();
@@ -182,38 +285,50 @@ __global__ void __launch_bounds__(kBlock, 4) serve_kernel(ServeCtl ctl)
             cached = best_block;
         }
         const Scratch sc = load_scratch(&b->sc);
-        LaneStats st;
-        if (kind == 1) {
-            PairConsts P = fd.p2;
-            if (fd.axis_slice)
-                march2_tile<0, 0, false, true>(fd, P, sc, item, st);
-            else
-                march2_tile<0, 0, false, false>(fd, P, sc, item, st);
-            flush_lane_stats<false>(sc, st, true);
-            __threadfence();
-            unsigned long long done = 0;
-            if (lane == 0) done = atomicAdd(&b->tile_done, 1ull) + 1ull;
-            done = __shfl_sync(kFull, done, 0);
-            if (lane == 0 && done == (unsigned long long)__ldcg(&b->ntiles)) {
-                const unsigned nh = min(ld_vol32(&b->ctr.hit_count), sc.hit_cap);
-                *reinterpret_cast<volatile unsigned *>(&b->hit_total) = nh;
-                __threadfence();
-                if (nh == 0)
-                    finish_request(b, ctl, fd.stats);
+        const bool recheck = fd.precision == DQJ_FP32_RECHECK;
+        unsigned long long *done_ctr;
+        unsigned n_items, total;
+        if (ph == kPhaseMarch) {
+            if (recheck) {
+                if (fd.axis_slice)
+                    march_item<true, true>(fd, sc, item, s_stage[wib]);
                 else
-                    st_release(&b->phase, kPhaseBisect);
+                    march_item<true, false>(fd, sc, item, s_stage[wib]);
+            } else {
+                if (fd.axis_slice)
+                    march_item<false, true>(fd, sc, item, nullptr);
+                else
+                    march_item<false, false>(fd, sc, item, nullptr);
             }
-        } else {
+            done_ctr = &b->tile_done;
+            n_items = 1;
+            total = __ldcg(&b->ntiles);
+        } else if (ph == kPhaseBisect) {
             const unsigned nh = ld_vol32(&b->hit_total);
-            bisect_chunk<float, 0, 0, false>(fd, sc, item, nh, st);
-            flush_lane_stats<false>(sc, st, false);
-            __threadfence();
-            const unsigned n = min(32u, nh - item);
-            unsigned long long done = 0;
-            if (lane == 0) done = atomicAdd(&b->hit_done, (unsigned long long)n) + n;
-            done = __shfl_sync(kFull, done, 0);
-            if (lane == 0 && done == (unsigned long long)nh) finish_request(b, ctl, fd.stats);
+            if (recheck)
+                bisect_item<true>(fd, sc, item, nh);
+            else
+                bisect_item<false>(fd, sc, item, nh);
+            done_ctr = &b->hit_done;
+            n_items = min(32u, nh - item);
+            total = nh;
+        } else if (ph == kPhaseRecheck) {
+            const unsigned nq = ld_vol32(&b->q_total);
+            recheck_item(fd, sc, item, nq);
+            done_ctr = &b->q_done;
+            n_items = min(32u, nq - item);
+            total = nq;
+        } else {
+            fixup_item(fd, sc, item);
+            done_ctr = &b->f_done;
+            n_items = 1;
+            total = ld_vol32(&b->f_total);
         }
+        __threadfence();
+        unsigned long long done = 0;
+        if (lane == 0) done = atomicAdd(done_ctr, (unsigned long long)n_items) + n_items;
+        done = __shfl_sync(kFull, done, 0);
+        if (lane == 0 && done == (unsigned long long)total) next_phase(b, ctl, fd, ph);
     }
 }
 

@@ -10,7 +10,11 @@ constexpr int kMaxSlots = 64;        // requests resident on the device at once
 constexpr int kReqBlocks = 1024;     // request control blocks (see ReqBlock)
 constexpr int DQJ_NSTATS_DEV = 10;   // = DQJ_NSTATS
 
-enum : unsigned { kPhaseMarch = 0, kPhaseBisect = 1, kPhaseDone = 2 };
+// A request's phases, in order.  FP32 + FP64 recheck requests pass through
+// kPhaseRecheck (FP64 recheck of the queued samples) and kPhaseFixup (FP64
+// re-render of the pixels whose FP64 escape count differed); each phase is
+// skipped when it has no work.
+enum : unsigned { kPhaseMarch = 0, kPhaseBisect = 1, kPhaseRecheck = 2, kPhaseFixup = 3, kPhaseDone = 4 };
 
 // Control block of one admitted request.  Written by the host before the
 // request is published and, apart from its counters, never changed afterwards.
@@ -27,7 +31,11 @@ struct alignas(128) ReqBlock {
     unsigned hit_total;             // hit-list length, set when the march completes
     unsigned slot;                  // slot the request occupies
     unsigned gen;                   // generation reported through the slot's done flag
-    unsigned pad[3];
+    unsigned recheck;               // 1: FP32 + FP64 recheck request
+    unsigned q_total;               // recheck-queue length, set when the bisection completes
+    unsigned f_total;               // re-render list length, set when the recheck completes
+    unsigned long long q_claim, q_done;  // recheck queue entries claimed / completed
+    unsigned long long f_claim, f_done;  // re-rendered pixels claimed / completed
     Counters ctr;                   // the request's counters (stats, hit_count)
     Scratch sc;                     // sc.ctr = &ctr; sc.hits = the slot's hit buffer
     FrameDesc fd;                   // frame constants and caller's output planes
@@ -48,6 +56,7 @@ struct ServeCtl {
     unsigned *done_flags;           // mapped host memory: generation of the last finished request per slot
     unsigned *exit_flag;            // device memory, 0 at launch: non-zero makes every warp exit
     unsigned *hold;                 // mapped host memory: non-zero while the host has queued or running work
+    unsigned long long *times;      // mapped host memory: per slot {first item claimed, finished}, %globaltimer ns
     unsigned long long idle_ns;     // a warp with no work (and no hold) for this long ends the launch
     unsigned long long hold_ns;     // ... and with hold set, after this long regardless
 };

@@ -1,6 +1,7 @@
 """Served form on the GPU: requests of different sizes, constants, iteration
-limits and slice frames run together in the persistent launch (or, for other
-precisions and modes, as frames on the serving stream).  Every result must be
+limits, slice frames and both FP32 modes (plain, and FP32 + FP64 recheck) run
+together in the persistent launch (other precisions and modes as frames on the
+serving stream).  Every result must be
 identical to rendering the same request alone with dqj_render, whatever else was
 in the mix.  Budget-limited admission and a long stream of small requests are
 covered too."""
@@ -55,6 +56,12 @@ def mixed_requests():
         reqs.append(s)
     reqs.append(scenes.default_scene(width=1, height=1))
     reqs.append(scenes.default_scene(width=37, height=19))
+    # the contract-accurate mode in the same launch: FP32 + FP64 recheck of an
+    # axis frame, general slices and the 1080p workload frame
+    for i in (0, 2, 4, 9):
+        reqs.append(dict(reqs[i], precision=scenes.PRECISION_FP32_RECHECK))
+    reqs.append(dict(scenes.default_scene(width=300, height=200, max_iter=16, march_steps=512, bisect_steps=10),
+                     precision=scenes.PRECISION_FP32_RECHECK))
     return reqs
 
 
@@ -68,9 +75,16 @@ def test_served_equals_alone(policy):
             binding.dqj_serve_policy(ctx, policy)
             outs, status = run_served(ctx, reqs)
             assert all(v == binding.DQJ_OK for v in status.values()), status
+            # every request ran in the persistent launch, the launch served
+            # several at once, and their device executions overlapped
+            stats = binding.dqj_serve_stats(ctx)
+            assert stats["packed"] == len(reqs) and stats["plain"] == 0, stats
+            assert stats["launches"] < len(reqs), stats
+            assert stats["max_active"] >= 2, stats
+            assert stats["overlapped"] >= 1, stats
             for i, s in enumerate(reqs):
                 alone = rdr.render(s)
-                assert_same(outs[i], alone, s, f"request {i}")
+                assert_same(outs[i], alone, s, f"request {i} precision {s['precision']}")
         finally:
             binding.dqj_destroy(ctx)
     torch.cuda.synchronize()

@@ -185,4 +185,68 @@ def test_serve_stats_count_admissions_and_completions(mock_env):
     st = binding.dqj_serve_stats(ctx)
     assert st["completed"] == 7 and st["plain"] == 7 and st["packed"] == 0  # the mock runs no persistent launch
     assert 1 <= st["batches"] <= 7 and st["launches"] == 0 and st["loops"] >= st["batches"]
+    # seven requests submitted together, each running 1 ms on the mock, were resident together
+    assert 2 <= st["max_active"] <= 7 and st["overlapped"] == 0, st
+    binding.dqj_destroy(ctx)
+
+
+def test_shortest_policy_orders_the_host_queue(mock_env):
+    """DQJ_SERVE_SHORTEST also orders the host queue: with the budget taken by a
+    running request, a 1920x1080 request and two 16x16 requests submitted just
+    after it are admitted smallest estimated finish first (FIFO: arrival order)."""
+    mock_env.setenv("DQJ_MOCK_DELAY_US", "20000")
+    big = scenes.default_scene(width=1920, height=1080, march_steps=512)
+    small = scenes.default_scene(width=16, height=16, march_steps=512)
+    orders = {}
+    for policy in (binding.DQJ_SERVE_FIFO, binding.DQJ_SERVE_SHORTEST):
+        ctx = binding.dqj_create(MOCK, mem_budget_bytes=footprint(big) + 2 * footprint(small))
+        binding.dqj_serve_policy(ctx, policy)
+        blocker = binding.dqj_submit(ctx, big, binding.make_outputs(pitch_px=1920))
+        time.sleep(0.005)  # the blocker is admitted and holds the budget
+        a = binding.dqj_submit(ctx, big, binding.make_outputs(pitch_px=1920))
+        b = binding.dqj_submit(ctx, small, binding.make_outputs(pitch_px=16))
+        c = binding.dqj_submit(ctx, small, binding.make_outputs(pitch_px=16))
+        order, res = wait_all(ctx, [blocker, a, b, c])
+        assert all(v == binding.DQJ_OK for v in res.values())
+        orders[policy] = [{blocker: "blocker", a: "big", b: "small1", c: "small2"}[t] for t in order]
+        binding.dqj_destroy(ctx)
+    assert orders[binding.DQJ_SERVE_FIFO] == ["blocker", "big", "small1", "small2"], orders
+    assert orders[binding.DQJ_SERVE_SHORTEST][0] == "blocker", orders
+    assert orders[binding.DQJ_SERVE_SHORTEST][-1] == "big", orders
+
+
+@pytest.mark.parametrize("policy", [binding.DQJ_SERVE_FIFO, binding.DQJ_SERVE_SHORTEST])
+def test_tight_polling_does_not_starve_the_scheduler(mock_env, policy):
+    """A client that polls every in-flight ticket in a loop without sleeping
+    (the benchmark's pattern) while requests keep arriving: dqj_poll does not
+    take the scheduler's lock, so admissions and completions keep going."""
+    import numpy as np
+    mock_env.setenv("DQJ_MOCK_DELAY_US", "200")
+    ctx = binding.dqj_create(MOCK)
+    binding.dqj_serve_policy(ctx, policy)
+    sizes = [(16, 16), (64, 64), (256, 256)]
+    reqs = [scenes.default_scene(width=w, height=h) for w, h in sizes]
+    rng = np.random.default_rng(3)
+    n = 3000
+    arrivals = np.cumsum(rng.exponential(50e-6, n))
+    kinds = rng.integers(0, len(sizes), n)
+    t0 = time.perf_counter()
+    nxt, inflight, done_n = 0, {}, 0
+    while nxt < n or inflight:
+        now = time.perf_counter() - t0
+        while nxt < n and arrivals[nxt] <= now:
+            k = int(kinds[nxt])
+            t = binding.dqj_submit(ctx, reqs[k], binding.make_outputs(pitch_px=sizes[k][0]))
+            inflight[t] = k
+            nxt += 1
+        for t in list(inflight):
+            done, st = binding.dqj_poll(ctx, t)
+            if done:
+                assert st == binding.DQJ_OK
+                inflight.pop(t)
+                done_n += 1
+        assert time.perf_counter() - t0 < 20.0, (nxt, len(inflight), binding.dqj_serve_stats(ctx))
+    assert done_n == n
+    st = binding.dqj_serve_stats(ctx)
+    assert st["completed"] == n and st["loops"] > 0
     binding.dqj_destroy(ctx)
