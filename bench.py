@@ -436,6 +436,11 @@ def run_gpu(args, world, rank, local):
         line["precision_report"] = precision_section(local)
     if not args.no_serve:
         line["served"] = serving_section(local, n_sat=512, n_stream=args.requests, rates=(0.8, 1.0))
+        rq = serving_section(local, n_sat=512, n_stream=0, rates=(), policies=(), precision=1)
+        line["served_recheck"] = {k: rq[k] for k in ("requests_burst", "served_frames_per_s",
+                                                     "plain_back_to_back_frames_per_s", "served_over_plain",
+                                                     "burst_scheduler")}
+        line["served_recheck"]["mode"] = MODE_NAMES[1]
         line["batch64"] = batch_section(local)
 
     line["c1"] = c1_section(local)
@@ -556,16 +561,17 @@ def pct(v, q):
 POLICY_NAMES = {0: "fifo", 1: "shortest"}
 
 
-def serving_section(local, n_sat=256, n_stream=600, rates=(0.8, 1.0), policies=(0, 1)):
+def serving_section(local, n_sat=256, n_stream=600, rates=(0.8, 1.0), policies=(0, 1), precision=0):
     """Served vs back-to-back frames/s on a burst of the serving mix, then Poisson
     arrivals at the given fractions of the measured saturation rate, under each
-    serving policy (admission order; earliest estimated finish), with latency
-    percentiles overall and per request size."""
+    serving policy (arrival order; earliest estimated finish), with latency
+    percentiles (and their sample counts) overall and per request size.  All
+    requests in the given precision mode."""
     import numpy as np
     import torch
 
     from paper_2303_14827_gb300 import binding, scenes
-    stream_reqs = [s for _, s in scenes.serving_stream(seed=2, n=max(n_sat, n_stream))]
+    stream_reqs = [s for _, s in scenes.serving_stream(seed=2, n=max(n_sat, n_stream), precision=precision)]
     pool = OutputPool(f"cuda:{local}")
     ctx = binding.dqj_create(local)
     try:
@@ -598,7 +604,8 @@ def serving_section(local, n_sat=256, n_stream=600, rates=(0.8, 1.0), policies=(
                     by_size["%dx%d" % wh] = {"n": len(ls), "p50_ms": round(1e3 * pct(ls, 0.50), 3),
                                              "p99_ms": round(1e3 * pct(ls, 0.99), 3)}
                 out["poisson"].append({"policy": POLICY_NAMES[policy], "offered_fraction_of_saturation": f,
-                                       "requests": len(reqs), "p50_ms": 1e3 * pct(lat, 0.50),
+                                       "requests": len(reqs), "latency_samples": len(lat),
+                                       "p50_ms": 1e3 * pct(lat, 0.50),
                                        "p99_ms": 1e3 * pct(lat, 0.99), "achieved_frames_per_s": len(reqs) / span,
                                        "by_size": by_size})
         binding.dqj_serve_policy(ctx, binding.DQJ_SERVE_FIFO)

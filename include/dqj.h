@@ -388,7 +388,12 @@ dqj_status dqj_render_voxels(dqj_ctx *ctx, const dqj_params *p, int32_t grid_n, 
  * p, out and cuda_stream as for dqj_render: out holds caller-owned DEVICE planes
  * (and an optional device stats array).  Runs on the current device; the first
  * call on each device looks up the array's device address with
- * cudaGetSymbolAddress, so make that first call before any stream capture.
+ * cudaGetSymbolAddress.  Under lazy module loading (the CUDA default) that
+ * first call is also when the array is placed on the device, so make it before
+ * reserving the device's memory for your own pool, and before any stream
+ * capture.  The address is kept for the life of the process: cudaDeviceReset
+ * after the first call is not supported.  The march kernel and tile shape are
+ * dqj_render's defaults (no autotuned shapes: there is no context).
  * Stream-ordered: enqueues and returns.  Allocates nothing (no cudaMalloc,
  * cudaFree or allocating library routine).  Errors: DQJ_ERR_INVALID when
  * width * height > DQJ_NOALLOC_MAX_PIXELS or precision is DQJ_FP32_RECHECK

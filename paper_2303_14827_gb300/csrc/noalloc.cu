@@ -5,12 +5,17 @@
 // this library, or a frame loop that must not block on the allocator.
 //
 // The array is DQJ_NOALLOC_MAX_PIXELS hit-list entries (16 B each) plus a
-// 256-byte counter block, about 4 MiB, and every device that loads the library
-// holds it until the process exits.  Its device address is looked up once per
-// device with cudaGetSymbolAddress, on the first call made while that device is
-// current; make that first call before any stream capture.  All calls share
-// the array: the counter block is cleared at the start of every call, and calls
-// that overlap on the GPU (other streams or threads) race on it.
+// 256-byte counter block, about 4 MiB.  Its device address is looked up once
+// per device with cudaGetSymbolAddress, on the first call made while that
+// device is current.  Under lazy module loading (the CUDA default) that first
+// call is also when the array is placed on the device, so make it before the
+// caller reserves the device's memory for its own pool and before any stream
+// capture; from then on the device holds the array until the process exits.
+// The address is kept for the life of the process: a cudaDeviceReset after the
+// first call is not supported.  All calls share the array: the counter block
+// is cleared at the start of every call, and calls that overlap on the GPU
+// (other streams or threads) race on it.  The march kernel and tile shape are
+// dqj_render's defaults (default_tile_shape, DQJ_MARCH_VARIANT included).
 #include <mutex>
 
 #include "runtime.h"
@@ -80,10 +85,11 @@ extern "C" dqj_status dqj_render_noalloc(const dqj_params *p, const dqj_outputs 
         sc.hits = reinterpret_cast<int4 *>(static_cast<unsigned char *>(base) + kCounterBytes);
         sc.hit_cap = DQJ_NOALLOC_MAX_PIXELS;
 
-        const bool fp64 = p->precision == DQJ_FP64;
+        int variant, tw, th;
+        dqj::default_tile_shape(*p, variant, tw, th);
         dqj::FrameDesc fd;
-        dqj::derive_frame(*p, fd, 8, fp64 ? 4 : 8);
-        fd.march_variant = fp64 ? 0 : 1;
+        dqj::derive_frame(*p, fd, tw, th);
+        fd.march_variant = variant;
         fd.pitch = out->pitch_px;
         fd.iter = out->iter;
         fd.depth = out->depth;
@@ -92,6 +98,9 @@ extern "C" dqj_status dqj_render_noalloc(const dqj_params *p, const dqj_outputs 
         fd.epoch = 1;
 
         cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+        // launch errors are read back with cudaGetLastError: start from a clean
+        // slate, so an earlier failed call of the caller's is not taken for ours
+        (void)cudaGetLastError();
         e = cudaMemsetAsync(sc.ctr, 0, kCounterBytes, st);
         if (e != cudaSuccess) return dqj::cuda_fail(e, "render_noalloc: clear counters");
         e = dqj::launch_frame(fd, sc, st, sms);

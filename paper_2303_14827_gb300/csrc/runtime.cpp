@@ -355,13 +355,18 @@ dqj_status scratch_ensure(ScratchBuf &s, uint64_t pixels, bool need_queue)
 // else the paired kernel on 8 x 8 tiles (FP32) or one ray per lane on 8 x 4
 // (FP64).  The environment variable DQJ_MARCH_VARIANT (0 or 1) overrides the
 // FP32 kernel: 0 one ray per lane, 1 two rays per lane.
-void pick_tile_shape(dqj_ctx *ctx, const dqj_params &p, int &variant, int &tw, int &th)
+void default_tile_shape(const dqj_params &p, int &variant, int &tw, int &th)
 {
     variant = p.precision == DQJ_FP64 ? 0 : 1;
     if (const char *e = std::getenv("DQJ_MARCH_VARIANT"))
         if (e[0] == '0' || e[0] == '1') variant = p.precision == DQJ_FP64 ? 0 : e[0] - '0';
     tw = 8;
     th = variant >= 1 ? 8 : 4;
+}
+
+void pick_tile_shape(dqj_ctx *ctx, const dqj_params &p, int &variant, int &tw, int &th)
+{
+    default_tile_shape(p, variant, tw, th);
     const int64_t px = (int64_t)p.width * p.height;
     const int cls = px <= 65536 ? 0 : px <= 262144 ? 1 : px <= 1048576 ? 2 : 3;
     const int bucket = p.max_iter <= 12 ? 0 : p.max_iter <= 20 ? 1 : p.max_iter <= 28 ? 2 : 3;

@@ -94,6 +94,10 @@ struct dqj_ctx {
 namespace dqj {
 // March kernel variant and tile shape for a frame (autotuned choice or default).
 void pick_tile_shape(dqj_ctx *ctx, const dqj_params &p, int &variant, int &tw, int &th);
+// The default choice without a context: the paired kernel on 8 x 8 tiles (FP32)
+// or one ray per lane on 8 x 4 (FP64), DQJ_MARCH_VARIANT (0 or 1) overriding
+// the FP32 kernel.
+void default_tile_shape(const dqj_params &p, int &variant, int &tw, int &th);
 // Autotuner cache (autotune.cpp): key of a (variant, size class, iteration bucket)
 // and loading of the cache file named by the context or DQJ_AUTOTUNE_CACHE.
 int tile_key(int variant, int size_class, int bucket);

@@ -57,3 +57,31 @@ def test_noalloc_fp64_and_limits():
         binding.dqj_render_noalloc(scenes.default_scene(precision=scenes.PRECISION_FP32_RECHECK),
                                    binding.make_outputs(pitch_px=256), 0)
     assert ei.value.status == binding.DQJ_ERR_INVALID and "DQJ_FP64 only" in str(ei.value)
+
+
+def test_noalloc_distance_estimate_traversal_and_no_allocation():
+    """The sphere-tracing traversal through the fixed array equals dqj_render, and
+    a call after a warm-up of the same kind changes neither the device's free
+    memory nor torch's allocations: the entry point allocates nothing.  (The
+    warm-up comes first because under lazy module loading the first launch of a
+    kernel loads its code.)"""
+    import torch
+    with binding.Renderer(0) as rdr:
+        s = scenes.default_scene(width=160, height=120, traversal=scenes.TRAVERSAL_DE)
+        ref, out = _both(rdr, s)
+        a, b = to_numpy(ref, 160, 120), to_numpy(out, 160, 120)
+        for k in ("iter", "depth", "normal", "rgba"):
+            assert np.array_equal(a[k], b[k]), k
+        assert binding.stats_dict(ref["stats"]) == binding.stats_dict(out["stats"])
+        march = scenes.default_scene(width=200, height=144)
+        o2 = binding.alloc_outputs(200, 144)
+        stream = torch.cuda.current_stream()
+        for sc, o in ((s, out), (march, o2)):  # warm-up of both kinds
+            binding.dqj_render_noalloc(sc, binding.outputs_of(o), stream.cuda_stream)
+        torch.cuda.synchronize()
+        free0, torch0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
+        for sc, o in ((s, out), (march, o2)):
+            binding.dqj_render_noalloc(sc, binding.outputs_of(o), stream.cuda_stream)
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
+        assert torch.cuda.memory_allocated() == torch0
