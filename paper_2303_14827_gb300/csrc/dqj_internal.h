@@ -75,6 +75,8 @@ struct alignas(16) FrameDesc {
     int64_t *stats;   // served requests: caller's DQJ_NSTATS counters (device), or NULL
     uint32_t epoch;   // tag for per-pixel dirty flags, changes every frame
     uint32_t axis_slice;  // 1: slice origin and basis are zero in components 3..7
+    int32_t k_split;      // march samples split into this many ranges across warps (1: not split)
+    int32_t k_chunk;      // samples per range
 };
 
 // Counters at the head of the scratch block; zeroed before every frame.
@@ -101,6 +103,10 @@ struct alignas(16) Scratch {
     uint32_t *dirty_flag; // per pixel, == epoch when the pixel is queued for re-render
     int32_t *dirty_list;
     uint32_t dirty_cap;
+    int4 *part;           // split march: per range and pixel {first inside k or -1, iterations, max escape count, samples}
+    uint32_t *part_hit;   // split march: per pixel, the lowest range that found an inside sample (~0u: none yet)
+    uint32_t part_cap;    // entries of part
+    uint32_t pad_[3];
 };
 
 // Host-side launch helpers implemented in render.cu.
@@ -112,5 +118,8 @@ cudaError_t launch_frame(const FrameDesc &fd, const Scratch &sc, cudaStream_t st
 // shading of its hits; same events (the last three after the shading pass).
 cudaError_t launch_de(const FrameDesc &fd, const Scratch &sc, cudaStream_t st, int num_sms, cudaEvent_t *ev);
 cudaError_t fma_peak_launch(int variant, int num_sms, float *sink, cudaStream_t st, double *flops);
+// Ranges the paired FP32 march of a frame splits its samples into (1: none):
+// enough for the frame's tiles to fill the resident warps of num_sms SMs.
+int march_split(const FrameDesc &fd, int num_sms);
 
 }  // namespace dqj

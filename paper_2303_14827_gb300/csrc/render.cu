@@ -20,6 +20,7 @@
 // Iteration counts are the algorithmic ones (escape count, or max_iter for an
 // inside sample), accumulated per lane and added once per warp.
 #include <cstdio>
+#include <cstdlib>
 
 #include "render_common.cuh"
 #include "../../include/dqj.h"
@@ -141,6 +142,68 @@ __global__ void __launch_bounds__(kBlock, AXIS ? 5 : 4)  // the general form kee
 }
 
 // ---------------------------------------------------------------------------
+// split march, for frames with fewer tiles than the GPU has resident warps: a
+// work item is one 64-ray tile and one of fd.k_split contiguous ranges of the
+// samples, so that more warps share a small frame.  Ranges past a ray's first
+// inside sample do work the march would not do (less when an earlier range
+// has already recorded its hit: the ray is skipped); march_merge_kernel keeps
+// only the ranges up to the first inside sample, so outputs and iteration
+// counts are the march's.
+// ---------------------------------------------------------------------------
+template <int SQ, int MOD, bool AXIS>
+__global__ void __launch_bounds__(kBlock, AXIS ? 5 : 4) march2_split_kernel(const __grid_constant__ FrameDesc fd, const Scratch sc)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned items = (unsigned)fd.tiles_x * (unsigned)fd.tiles_y * (unsigned)fd.k_split;
+    for (;;) {
+        unsigned item = 0;
+        if (lane == 0) item = atomicAdd(&sc.ctr->tile_next, 1u);
+        item = __shfl_sync(kFull, item, 0);
+        if (item >= items) break;
+        // lower ranges first, so that later ones find the rays they can skip
+        const unsigned ntiles = (unsigned)fd.tiles_x * (unsigned)fd.tiles_y;
+        const unsigned r = item / ntiles, tile = item % ntiles;
+        const int kb = (int)r * fd.k_chunk, ke = min(kb + fd.k_chunk, fd.N + 1);
+        LaneStats st;
+        march2_tile<SQ, MOD, false, AXIS, true>(fd, fd.p2, sc, tile, st, nullptr, kb, ke);
+    }
+}
+
+// Per pixel: the ranges of the split march in sample order up to the first
+// with an inside sample give the pixel's result (a miss's largest escape count,
+// or the hit's first inside sample for the bisection pass) and its iterations
+// and samples.
+__global__ void __launch_bounds__(kBlock) march_merge_kernel(const __grid_constant__ FrameDesc fd, const Scratch sc)
+{
+    const int64_t npx = (int64_t)fd.W * fd.H;
+    LaneStats st;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < npx; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t pixel = base + threadIdx.x;
+        const bool part = pixel < npx;
+        int kf = -1, m = 0;
+        unsigned iters = 0, samples = 0;
+        for (int r = 0; part && r < fd.k_split; ++r) {
+            const int4 e = sc.part[(int64_t)r * npx + pixel];
+            iters += (unsigned)e.y;
+            samples += (unsigned)e.w;
+            if (e.x >= 0) {
+                kf = e.x;
+                break;
+            }
+            m = max(m, e.z);
+        }
+        const bool hit = kf >= 0;
+        st.iters += iters;
+        st.samples += samples;
+        st.hits += hit ? 1 : 0;
+        const int x = (int)(pixel % fd.W), y = (int)(pixel / fd.W);
+        if (part && !hit) write_miss<float>(fd, x, y, m);
+        warp_push(hit, make_int4((int)pixel, kf, 0, 0), sc.hits, sc.hit_cap, &sc.ctr->hit_count);
+    }
+    flush_lane_stats<false>(sc, st, true);
+}
+
+// ---------------------------------------------------------------------------
 // bisect + normal + shade over the hit list
 // ---------------------------------------------------------------------------
 template <typename T, int SQ, int MOD, bool RECHECK>
@@ -196,8 +259,24 @@ cudaError_t launch_passes(const FrameDesc &fd, const Scratch &sc, cudaStream_t s
     static std::atomic<int> g_march{0}, g_march2a{0}, g_march2g{0}, g_bisect{0};
     const unsigned ntiles = (unsigned)fd.tiles_x * (unsigned)fd.tiles_y;
     if (ev) cudaEventRecord(ev[0], st);
+    if constexpr (sizeof(T) == 4 && !RECHECK) {
+        if (fd.march_variant == 1 && fd.k_split > 1) {
+            static std::atomic<int> g_sa{0}, g_sg{0}, g_mg{0};
+            const unsigned items = ntiles * (unsigned)fd.k_split;
+            if (fd.axis_slice) {
+                const int cap = num_sms * resident_per_sm(g_sa, march2_split_kernel<SQ, MOD, true>);
+                march2_split_kernel<SQ, MOD, true><<<(int)min((unsigned)cap, (items + 3u) / 4u), kBlock, 0, st>>>(fd, sc);
+            } else {
+                const int cap = num_sms * resident_per_sm(g_sg, march2_split_kernel<SQ, MOD, false>);
+                march2_split_kernel<SQ, MOD, false><<<(int)min((unsigned)cap, (items + 3u) / 4u), kBlock, 0, st>>>(fd, sc);
+            }
+            const unsigned npx = (unsigned)fd.W * (unsigned)fd.H;
+            const int capm = num_sms * resident_per_sm(g_mg, march_merge_kernel);
+            march_merge_kernel<<<(int)min((unsigned)capm, (npx + kBlock - 1) / kBlock), kBlock, 0, st>>>(fd, sc);
+        }
+    }
     if constexpr (sizeof(T) == 4) {
-        if (fd.march_variant == 1) {
+        if (fd.march_variant == 1 && !(fd.k_split > 1 && !RECHECK)) {
             // a persistent grid per instantiation: the axis and general forms
             // have different register counts and resident CTAs per SM
             if (fd.axis_slice) {
@@ -246,6 +325,23 @@ cudaError_t launch_mode(const FrameDesc &fd, const Scratch &sc, cudaStream_t st,
 }
 
 }  // namespace
+
+int march_split(const FrameDesc &fd, int num_sms)
+{
+    static std::atomic<int> g_occ{0};
+    if (fd.precision != DQJ_FP32 || fd.march_variant != 1 || fd.traversal != DQJ_TRAVERSAL_MARCH) return 1;
+    if (const char *e = std::getenv("DQJ_MARCH_SPLIT")) {  // 0: never split; n > 1: n ranges
+        const long n = std::strtol(e, nullptr, 10);
+        if (n <= 1) return 1;
+        return (int)std::min<long>(std::min<long>(n, 64), (long)fd.N + 1);
+    }
+    const long long warps = (long long)num_sms * resident_per_sm(g_occ, march2_split_kernel<0, 0, true>) * (kBlock / 32);
+    const long long tiles = (long long)fd.tiles_x * fd.tiles_y;
+    if (tiles >= warps) return 1;
+    // about four waves of items: later waves skip the rays earlier ranges hit
+    const long long p = (4 * warps + tiles - 1) / tiles;
+    return (int)std::min<long long>(std::min<long long>(p, 16), (long long)fd.N + 1);
+}
 
 cudaError_t launch_frame(const FrameDesc &fd, const Scratch &sc, cudaStream_t st, int num_sms, cudaEvent_t *ev)
 {

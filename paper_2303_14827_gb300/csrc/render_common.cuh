@@ -449,10 +449,15 @@ __device__ __forceinline__ void recheck_staged(const FrameDesc &fd, const Scratc
 
 // One 64-ray tile of the paired march (see march2_kernel); all 32 lanes call.
 // A lane holds tile slots `lane` and `lane + 32`.  RECHECK: qs is the warp's
-// staging buffer of kQStage entries in shared memory.
-template <int SQ, int MOD, bool RECHECK, bool AXIS = false>
+// staging buffer of kQStage entries in shared memory.  SPLIT: only samples
+// [kb, ke) of each ray, with the range's partial result written to sc.part
+// (range r = kb / fd.k_chunk) for march_merge_kernel instead of the outputs;
+// a ray for which a lower range has already found an inside sample is
+// skipped (the merge stops at that range), and a range that finds one records
+// itself in sc.part_hit.
+template <int SQ, int MOD, bool RECHECK, bool AXIS = false, bool SPLIT = false>
 __device__ __forceinline__ void march2_tile(const FrameDesc &fd, const PairConsts &P, const Scratch &sc, unsigned tile,
-                                            LaneStats &st, int4 *qs = nullptr)
+                                            LaneStats &st, int4 *qs = nullptr, int kb = 0, int ke = 0)
 {
     const FrameT<float> &F = fd.f;
     const int lane = threadIdx.x & 31;
@@ -463,7 +468,7 @@ __device__ __forceinline__ void march2_tile(const FrameDesc &fd, const PairConst
     auto px = [&](int slot) { return tx * fd.tile_w + slot % fd.tile_w; };
     auto py = [&](int slot) { return ty * fd.tile_h + slot / fd.tile_w; };
     int pixa = 0, pixb = 0;
-    bool acta, actb;
+    bool acta, actb, skipa = false, skipb = false;
     // Axis-aligned slice: zeta_0 = A + t D (components 0..2).  Otherwise the
     // first-iterate form (first_iterate_coeffs): zeta_1 = Q0 + s (Q1 + s Q2),
     // s = t + dot, with Q0 kept in D and t + dot in tin.
@@ -480,6 +485,13 @@ __device__ __forceinline__ void march2_tile(const FrameDesc &fd, const PairConst
         float tia = 0.f, toa = 0.f, tib = 0.f, tob = 0.f;
         acta = va && camera_clip<float>(F, fd.W, fd.H, xa, ya, da, tia, toa);
         actb = vb && camera_clip<float>(F, fd.W, fd.H, xb, yb, db, tib, tob);
+        if constexpr (SPLIT) {
+            const unsigned r = (unsigned)(kb / fd.k_chunk);
+            skipa = va && __ldcg(sc.part_hit + ya * fd.W + xa) < r;
+            skipb = vb && __ldcg(sc.part_hit + yb * fd.W + xb) < r;
+            acta = acta && !skipa;
+            actb = actb && !skipb;
+        }
         if (!acta) tia = toa = 0.f;
         if (!actb) tib = tob = 0.f;
         dl = make_float2((toa - tia) / (float)N, (tob - tib) / (float)N);
@@ -511,11 +523,12 @@ __device__ __forceinline__ void march2_tile(const FrameDesc &fd, const PairConst
     const bool boxa = acta, boxb = actb;
     int suma = 0, sumb = 0, maxa = 0, maxb = 0, kfa = -1, kfb = -1;
     int qn = 0;  // staged recheck entries (warp-uniform)
-    float2 kf = make_float2(0.f, 0.f);
+    const int k0 = SPLIT ? kb : 0, k1 = SPLIT ? ke : N + 1;
+    float2 kf = make_float2((float)k0, (float)k0);
     // `more`: some ray of the warp still marches.  It changes only in a round
     // that found a ray inside, so it is voted on only then.
     bool more = __any_sync(kFull, acta || actb);
-    for (int k = 0; k <= N && more; ++k) {
+    for (int k = k0; k < k1 && more; ++k) {
         const float2 t = f2fma(kf, dl, tin);
         kf = f2add(kf, make_float2(1.f, 1.f));
         float2 z[8];
@@ -565,7 +578,25 @@ __device__ __forceinline__ void march2_tile(const FrameDesc &fd, const PairConst
     const bool hita = kfa >= 0, hitb = kfb >= 0;
     // iterations = sum of (escape count) over escaped samples + max_iter per inside sample
     //            = sum of bounded steps + number of escaped samples
-    const int nesca = hita ? kfa : N + 1, nescb = hitb ? kfb : N + 1;
+    const int nesca = (hita ? kfa : k1) - k0, nescb = (hitb ? kfb : k1) - k0;
+    if constexpr (SPLIT) {  // this range's partial result per ray (see march_merge_kernel)
+        const int xa = px(lane), ya = py(lane), xb = px(lane + 32), yb = py(lane + 32);
+        const unsigned r = (unsigned)(kb / fd.k_chunk);
+        const int64_t npx = (int64_t)fd.W * fd.H, base = (int64_t)r * npx;
+        if (xa < fd.W && ya < fd.H && !skipa) {
+            const int pa = ya * fd.W + xa;
+            sc.part[base + pa] = boxa ? make_int4(kfa, suma + nesca, maxa + 1, nesca + (hita ? 1 : 0))
+                                      : make_int4(-1, 0, 0, 0);
+            if (hita) atomicMin(sc.part_hit + pa, r);
+        }
+        if (xb < fd.W && yb < fd.H && !skipb) {
+            const int pb = yb * fd.W + xb;
+            sc.part[base + pb] = boxb ? make_int4(kfb, sumb + nescb, maxb + 1, nescb + (hitb ? 1 : 0))
+                                      : make_int4(-1, 0, 0, 0);
+            if (hitb) atomicMin(sc.part_hit + pb, r);
+        }
+        return;
+    }
     st.iters += (boxa ? suma + nesca : 0) + (boxb ? sumb + nescb : 0);
     st.samples += (boxa ? nesca + (hita ? 1 : 0) : 0) + (boxb ? nescb + (hitb ? 1 : 0) : 0);
     st.hits += (hita ? 1 : 0) + (hitb ? 1 : 0);

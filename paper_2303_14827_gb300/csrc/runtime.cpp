@@ -295,6 +295,8 @@ void derive_frame(const dqj_params &p, FrameDesc &fd, int tile_w, int tile_h)
     fd.tile_h = tile_h;
     fd.tiles_x = (p.width + tile_w - 1) / tile_w;
     fd.tiles_y = (p.height + tile_h - 1) / tile_h;
+    fd.k_split = 1;
+    fd.k_chunk = fd.N + 1;
 }
 
 static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -305,12 +307,14 @@ void scratch_free(ScratchBuf &s)
     s = ScratchBuf{};
 }
 
-dqj_status scratch_ensure(ScratchBuf &s, uint64_t pixels, bool need_queue)
+dqj_status scratch_ensure(ScratchBuf &s, uint64_t pixels, bool need_queue, uint64_t part_entries)
 {
-    if (s.base && pixels <= s.pixels && (!need_queue || s.with_queue)) return DQJ_OK;
+    if (s.base && pixels <= s.pixels && (!need_queue || s.with_queue) && part_entries <= s.part_entries)
+        return DQJ_OK;
     const uint64_t px = std::max<uint64_t>(pixels, s.pixels);
     const bool wq = need_queue || s.with_queue;
     const uint64_t qcap = wq ? 4 * px : 0;
+    const uint64_t pcap = std::max<uint64_t>(part_entries, s.part_entries);
     size_t off = 0;
     const size_t o_ctr = off;
     off = align_up(off + sizeof(Counters), 256);
@@ -322,6 +326,10 @@ dqj_status scratch_ensure(ScratchBuf &s, uint64_t pixels, bool need_queue)
     off = align_up(off + px * sizeof(uint32_t), 256);
     const size_t o_list = off;
     off = align_up(off + px * sizeof(int32_t), 256);
+    const size_t o_part = off;
+    off = align_up(off + pcap * sizeof(int4), 256);
+    const size_t o_phit = off;
+    off = align_up(off + (pcap ? px * sizeof(uint32_t) : 0), 256);
     void *base = nullptr;
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(e, "scratch: synchronize");
@@ -348,6 +356,10 @@ dqj_status scratch_ensure(ScratchBuf &s, uint64_t pixels, bool need_queue)
     s.view.dirty_flag = reinterpret_cast<uint32_t *>(b + o_flag);
     s.view.dirty_list = reinterpret_cast<int32_t *>(b + o_list);
     s.view.dirty_cap = (uint32_t)px;
+    s.part_entries = pcap;
+    s.view.part = pcap ? reinterpret_cast<int4 *>(b + o_part) : nullptr;
+    s.view.part_hit = pcap ? reinterpret_cast<uint32_t *>(b + o_phit) : nullptr;
+    s.view.part_cap = (uint32_t)pcap;
     return DQJ_OK;
 }
 
@@ -412,11 +424,16 @@ static dqj_status enqueue_frame(dqj_ctx *ctx, const dqj_params &p, const dqj_out
     if (e != cudaSuccess) return cuda_fail(e, "render: cudaStreamGetCaptureInfo");
     const bool capturing = cap == cudaStreamCaptureStatusActive;
     const bool recheck = p.precision == DQJ_FP32_RECHECK;
+    // a frame with fewer tiles than resident warps splits its samples into ranges
+    fd.k_split = march_split(fd, ctx->num_sms);
+    fd.k_chunk = (fd.N + 1 + fd.k_split - 1) / fd.k_split;
+    fd.k_split = (fd.N + 1 + fd.k_chunk - 1) / fd.k_chunk;  // every range holds a sample
+    const uint64_t part = fd.k_split > 1 ? (uint64_t)fd.k_split * px : 0;
     ScratchBuf &sb = ctx->scratch;
-    if (capturing && !(sb.base && px <= sb.pixels && (!recheck || sb.with_queue)))
+    if (capturing && !(sb.base && px <= sb.pixels && (!recheck || sb.with_queue) && part <= sb.part_entries))
         return fail(DQJ_ERR_INVALID, "render: under stream capture the context's scratch must already fit the frame "
                                      "(render the largest frame once before capturing)");
-    dqj_status s = scratch_ensure(sb, px, recheck);
+    dqj_status s = scratch_ensure(sb, px, recheck, part);
     if (s != DQJ_OK) return s;
     if (capturing) {
         if (recheck) {
@@ -440,6 +457,10 @@ static dqj_status enqueue_frame(dqj_ctx *ctx, const dqj_params &p, const dqj_out
     }
     e = cudaMemsetAsync(sb.view.ctr, 0, sizeof(Counters), st);
     if (e != cudaSuccess) return cuda_fail(e, "render: clear counters");
+    if (fd.k_split > 1) {
+        e = cudaMemsetAsync(sb.view.part_hit, 0xff, px * sizeof(uint32_t), st);
+        if (e != cudaSuccess) return cuda_fail(e, "render: clear split-march hits");
+    }
     cudaEvent_t *ev = nullptr;
     if (ctx->ring_frames > 0) ev = &ctx->ev[5 * (ctx->ring_next++ % (uint64_t)ctx->ring_frames)];
     e = launch_frame(fd, sb.view, st, ctx->num_sms, ev);

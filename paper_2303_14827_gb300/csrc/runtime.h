@@ -48,10 +48,11 @@ struct ScratchBuf {
     size_t bytes = 0;
     uint32_t pixels = 0;
     bool with_queue = false;
+    uint64_t part_entries = 0;  // split-march partial results
     Scratch view{};
     uint32_t epoch = 0;
 };
-dqj_status scratch_ensure(ScratchBuf &s, uint64_t pixels, bool need_queue);
+dqj_status scratch_ensure(ScratchBuf &s, uint64_t pixels, bool need_queue, uint64_t part_entries = 0);
 void scratch_free(ScratchBuf &s);
 
 struct ServeState;  // serving loop, serve.cpp

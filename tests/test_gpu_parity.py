@@ -190,6 +190,31 @@ def test_march_variants_bitwise_equal(rdr, scene, monkeypatch):
         assert o["stats"] == outs[0]["stats"]
 
 
+@pytest.mark.parametrize("scene", ["single", "ragged", "random_slice", "max_iter40"])
+def test_split_march_equals_unsplit(rdr, scene, monkeypatch):
+    # Frames with fewer tiles than the GPU has resident warps split each ray's
+    # samples into ranges marched by different warps; the merge keeps the
+    # ranges up to the first inside sample, so images and iteration counts
+    # equal the unsplit march exactly.
+    if scene == "single":
+        s = scenes.default_scene()
+    elif scene == "ragged":
+        s = scenes.default_scene(width=131, height=77, march_steps=255)
+    elif scene == "random_slice":
+        s = dict(scenes.batch_scenes(seed=1, n=3)[2], width=200, height=150)
+    else:
+        s = scenes.default_scene(width=160, height=120, max_iter=40, march_steps=97)
+    monkeypatch.setenv("DQJ_MARCH_SPLIT", "0")
+    whole = gpu_render(rdr, s)
+    monkeypatch.delenv("DQJ_MARCH_SPLIT")
+    split = gpu_render(rdr, s)
+    for k in ("iter", "depth", "normal", "rgba"):
+        assert np.array_equal(split[k], whole[k]), k
+    assert split["stats"] == whole["stats"]
+    if scene in ("single", "ragged"):
+        run_parity(rdr, s, f"split march {scene}")
+
+
 def test_render_host_batch_equals_device_render(rdr):
     # host outputs through the double-buffered batch: every frame equals the
     # device render of the same scene, with ragged sizes and a host pitch
