@@ -918,8 +918,9 @@ def run_voxel_only(args, world, rank, local):
 def de_section(local, reps=5):
     """The paper's own traversal (distance-estimate sphere tracing, Eq.
     distfract2) against the fixed-step march on the same 1920x1080 scenes:
-    the five workload frames and the default c.  FP32; ms per frame (best of
-    reps, CUDA events), DQ iterations, samples and hit pixels."""
+    the five workload frames and the default c.  FP32, and both traversals in
+    the contract-accurate FP32 + FP64 recheck mode; ms per frame (best of reps,
+    CUDA events), DQ iterations, samples, hit pixels and FP64 re-renders."""
     import torch
 
     from paper_2303_14827_gb300 import binding, scenes
@@ -934,7 +935,9 @@ def de_section(local, reps=5):
     try:
         for name, base in frames:
             row = {"frame": name}
-            for tag, sc in (("march", base), ("de", dict(base, traversal=scenes.TRAVERSAL_DE))):
+            rc = dict(base, precision=scenes.PRECISION_FP32_RECHECK)
+            for tag, sc in (("march", base), ("de", dict(base, traversal=scenes.TRAVERSAL_DE)),
+                            ("march_recheck", rc), ("de_recheck", dict(rc, traversal=scenes.TRAVERSAL_DE))):
                 binding.dqj_render(ctx, sc, binding.outputs_of(o), stream.cuda_stream)
                 best = 1e30
                 for _ in range(reps):
@@ -945,8 +948,9 @@ def de_section(local, reps=5):
                     best = min(best, e0.elapsed_time(e1))
                 st = binding.stats_dict(o["stats"])
                 row[tag] = {"ms": round(best, 4), "iters": st["class_iters"] + st["normal_iters"],
-                            "samples": st["samples"], "hits": st["hits"]}
+                            "samples": st["samples"], "hits": st["hits"], "fixups": st["fixups"]}
             row["de_speedup"] = round(row["march"]["ms"] / row["de"]["ms"], 2)
+            row["de_recheck_speedup"] = round(row["march_recheck"]["ms"] / row["de_recheck"]["ms"], 2)
             rows.append(row)
     finally:
         binding.dqj_destroy(ctx)

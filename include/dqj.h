@@ -74,7 +74,12 @@ enum {
  * by de_step_scale times the estimate, and misses when it leaves the volume
  * or after de_max_steps samples.  A hit's depth is its sample's t and n* its
  * escape count (max_iter when inside); a miss reports the largest escape
- * count over its samples.  DE supports DQJ_FP32 and DQJ_FP64. */
+ * count over its samples.  DE supports every precision.  Its FP32 +
+ * FP64-recheck mode re-traces every hit pixel in FP64 (the FP32 trace's ray
+ * parameter accumulates the rounding of each estimate) and rechecks in FP64 the
+ * samples of the other pixels whose escape test came within the margin of R^2
+ * or whose estimate lies near de_epsilon, re-tracing in FP64 the pixels whose
+ * decisions could differ. */
 #define DQJ_TRAVERSAL_MARCH 0
 #define DQJ_TRAVERSAL_DE 1
 

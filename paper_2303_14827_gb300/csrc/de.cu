@@ -16,6 +16,7 @@
 // planes directly.
 #include "render_common.cuh"
 #include "runtime.h"
+#include "../../include/dqj.h"
 
 namespace dqj {
 
@@ -27,11 +28,14 @@ constexpr int kDeTileW = 8, kDeTileH = 4;
 // count (0 = inside) and, for an escaped sample, the distance estimate.  AXIS:
 // only z[0..2] are set (the rest are zero) and the first step takes the axis
 // form (same results).
+// dm returns the smallest |modulus - R^2| of the steps tested up to and
+// including the escaping one (the recheck's margin distance).
 template <typename T, int SQ, int MOD, bool AXIS>
-__device__ __forceinline__ int classify_de(T (&z)[8], const FrameT<T> &F, int max_iter, bool part, T &dist)
+__device__ __forceinline__ int classify_de(T (&z)[8], const FrameT<T> &F, int max_iter, bool part, T &dist, T &dm)
 {
     bool alive = part;
     int cnt = 0;
+    dm = tinf<T>();
     T sp, m;
     if (AXIS) {
         sp = dfma(z[2], z[2], z[1] * z[1]);
@@ -43,6 +47,7 @@ __device__ __forceinline__ int classify_de(T (&z)[8], const FrameT<T> &F, int ma
     T dr2 = T(4) * m, m_esc = T(0), dr2_esc = T(1);
     // the first step, peeled so that it can take the axis form
     m = AXIS ? dq_iter_axis_first<T, MOD>(z, z, sp, F.c) : dq_iter<T, SQ, MOD>(z, z, sp, F.c);
+    if (alive) dm = fmin(dm, fabs(m - F.R2));
     if (alive && !(m <= F.R2)) {
         m_esc = m;
         dr2_esc = dr2;
@@ -53,6 +58,7 @@ __device__ __forceinline__ int classify_de(T (&z)[8], const FrameT<T> &F, int ma
         for (int n = 1; n < max_iter; ++n) {
             dr2 = T(4) * m * dr2;
             m = dq_iter<T, SQ, MOD>(z, z, sp, F.c);
+            if (alive) dm = fmin(dm, fabs(m - F.R2));
             if (alive && !(m <= F.R2)) {
                 m_esc = m;
                 dr2_esc = dr2;
@@ -74,10 +80,95 @@ __device__ __forceinline__ int classify_de(T (&z)[8], const FrameT<T> &F, int ma
     return cnt + 1;
 }
 
-template <typename T, int SQ, int MOD, bool AXIS>
-__global__ void __launch_bounds__(kBlock) de_kernel(const __grid_constant__ FrameDesc fd, const Scratch sc)
+// Sphere tracing of one ray per lane (all 32 lanes call; `valid` = the lane
+// has a pixel): from the entry into the box (and the bounding sphere), sample,
+// stop at an inside sample or one whose estimate is below epsilon (a hit at
+// that sample), else advance by the step scale times the estimate; leaving the
+// volume or running out of steps is a miss.  Returns whether the ray hit, with
+// its depth, n*, the largest escape count over its samples, and its direction.
+// RECHECK (FP32): the FP32 trace's ray parameter accumulates the rounding of
+// every estimate, so its hit depth can differ from the FP64 trace's by more
+// than the depth tolerance: every hit pixel is queued for the FP64 re-trace.
+// For the others, samples whose escape test came within the margin of R^2 or
+// whose estimate lies within kDeEpsBand * epsilon of epsilon are queued for the
+// FP64 recheck, and a step that lands within kDeExitBand of the exit queues
+// the pixel for the FP64 re-trace directly.
+constexpr float kDeEpsBand = 0.02f;   // relative to epsilon
+constexpr float kDeExitBand = 1e-5f;  // scene units (relative above 1)
+
+template <typename T, int SQ, int MOD, bool AXIS, bool RECHECK>
+__device__ __forceinline__ bool de_trace_lane(const FrameDesc &fd, const Scratch &sc, int x, int y, bool valid,
+                                              LaneStats &st, T (&d)[3], T (&D)[8], T &depth, int &n_star,
+                                              int &esc_max)
 {
     const FrameT<T> &F = frame<T>(fd);
+    d[0] = d[1] = T(0);
+    d[2] = T(1);
+    T t0 = T(0), t1 = T(0);
+    bool act = valid && camera_clip<T>(F, fd.W, fd.H, x, y, d, t0, t1);
+    if (act && F.de_rb > T(0)) {  // bounding sphere about the origin
+        const T b = F.eye[0] * d[0] + F.eye[1] * d[1] + F.eye[2] * d[2];
+        const T c = F.eye[0] * F.eye[0] + F.eye[1] * F.eye[1] + F.eye[2] * F.eye[2] - F.de_rb * F.de_rb;
+        const T disc = b * b - c;
+        if (disc > T(0)) {
+            const T q = sqrt(disc);
+            t0 = max(t0, -b - q);
+            t1 = min(t1, -b + q);
+            act = t0 < t1;
+        } else {
+            act = false;
+        }
+    }
+    slice_dir<T>(F, d, D);
+    T t = t0;
+    depth = T(0);
+    int steps = 0;
+    esc_max = 0;
+    n_star = 0;
+    bool hit = false;
+    const int pixel = y * fd.W + x;
+    while (__any_sync(kFull, act)) {
+        T z[8];
+#pragma unroll
+        for (int i = 0; i < (AXIS ? 3 : 8); ++i) z[i] = dfma(t, D[i], F.A[i]);  // AXIS: the rest are 0
+        T dist, dm;
+        const int n = classify_de<T, SQ, MOD, AXIS>(z, F, fd.max_iter, act, dist, dm);
+        const bool stop = n == 0 || dist < F.de_eps;
+        if (RECHECK) {
+            const bool push = act && (dm <= F.margin || (n != 0 && fabs(dist - F.de_eps) <= T(kDeEpsBand) * F.de_eps));
+            // {pixel, step, t bits, FP32 escape count | FP32 stop decision << 16}
+            if (warp_push(push, make_int4(pixel, steps, __float_as_int((float)t), n | (stop ? 1 << 16 : 0)), sc.queue,
+                          sc.queue_cap, &sc.ctr->queue_count)) {
+                atomicAdd(&sc.ctr->stats[7], 1ull);
+                mark_dirty(fd, sc, pixel);
+            }
+            st.rechecks += push ? 1 : 0;
+        }
+        if (act) {
+            ++steps;
+            st.iters += n ? (unsigned)n : (unsigned)fd.max_iter;
+            if (n > esc_max) esc_max = n;
+            if (stop) {
+                hit = true;
+                depth = t;
+                n_star = n ? n : fd.max_iter;
+                act = false;
+            } else {
+                t = t + F.de_scale * dist;
+                act = steps < fd.de_max_steps && t <= t1;
+                if (RECHECK && fabs(t - t1) <= T(kDeExitBand) * max(T(1), fabs(t1))) mark_dirty(fd, sc, pixel);
+            }
+        }
+    }
+    st.samples += (unsigned)steps;
+    st.hits += hit ? 1 : 0;
+    if (RECHECK && hit) mark_dirty(fd, sc, pixel);
+    return hit;
+}
+
+template <typename T, int SQ, int MOD, bool AXIS, bool RECHECK>
+__global__ void __launch_bounds__(kBlock) de_kernel(const __grid_constant__ FrameDesc fd, const Scratch sc)
+{
     const int lane = threadIdx.x & 31;
     const int tiles_x = (fd.W + kDeTileW - 1) / kDeTileW;
     const unsigned ntiles = (unsigned)tiles_x * (unsigned)((fd.H + kDeTileH - 1) / kDeTileH);
@@ -90,50 +181,10 @@ __global__ void __launch_bounds__(kBlock) de_kernel(const __grid_constant__ Fram
         const int x = (int)(tile % (unsigned)tiles_x) * kDeTileW + lane % kDeTileW;
         const int y = (int)(tile / (unsigned)tiles_x) * kDeTileH + lane / kDeTileW;
         const bool valid = x < fd.W && y < fd.H;
-        T d[3] = {T(0), T(0), T(1)};
-        T t0 = T(0), t1 = T(0);
-        bool act = valid && camera_clip<T>(F, fd.W, fd.H, x, y, d, t0, t1);
-        if (act && F.de_rb > T(0)) {  // bounding sphere about the origin
-            const T b = F.eye[0] * d[0] + F.eye[1] * d[1] + F.eye[2] * d[2];
-            const T c = F.eye[0] * F.eye[0] + F.eye[1] * F.eye[1] + F.eye[2] * F.eye[2] - F.de_rb * F.de_rb;
-            const T disc = b * b - c;
-            if (disc > T(0)) {
-                const T q = sqrt(disc);
-                t0 = max(t0, -b - q);
-                t1 = min(t1, -b + q);
-                act = t0 < t1;
-            } else {
-                act = false;
-            }
-        }
-        T D[8];
-        slice_dir<T>(F, d, D);
-        T t = t0, depth = T(0);
-        int steps = 0, esc_max = 0, n_star = 0;
-        bool hit = false;
-        while (__any_sync(kFull, act)) {
-            T z[8];
-#pragma unroll
-            for (int i = 0; i < (AXIS ? 3 : 8); ++i) z[i] = dfma(t, D[i], F.A[i]);  // AXIS: the rest are 0
-            T dist;
-            const int n = classify_de<T, SQ, MOD, AXIS>(z, F, fd.max_iter, act, dist);
-            if (act) {
-                ++steps;
-                st.iters += n ? (unsigned)n : (unsigned)fd.max_iter;
-                if (n > esc_max) esc_max = n;
-                if (n == 0 || dist < F.de_eps) {
-                    hit = true;
-                    depth = t;
-                    n_star = n ? n : fd.max_iter;
-                    act = false;
-                } else {
-                    t = t + F.de_scale * dist;
-                    act = steps < fd.de_max_steps && t <= t1;
-                }
-            }
-        }
-        st.samples += (unsigned)steps;
-        st.hits += hit ? 1 : 0;
+        T d[3], D[8], depth;
+        int n_star, esc_max;
+        const bool hit = de_trace_lane<T, SQ, MOD, AXIS, RECHECK>(fd, sc, x, y, valid, st, d, D, depth, n_star,
+                                                                  esc_max);
         if (valid && !hit) write_miss<T>(fd, x, y, esc_max);
         int4 e = make_int4(y * fd.W + x, 0, 0, n_star);
         if constexpr (sizeof(T) == 8) {
@@ -143,9 +194,68 @@ __global__ void __launch_bounds__(kBlock) de_kernel(const __grid_constant__ Fram
         } else {
             e.y = __float_as_int((float)depth);
         }
-        warp_push(hit, e, sc.hits, sc.hit_cap, &sc.ctr->hit_count);
+        // RECHECK: hits are re-traced and shaded by de_fixup_kernel
+        warp_push(hit && !RECHECK, e, sc.hits, sc.hit_cap, &sc.ctr->hit_count);
     }
-    flush_lane_stats<false>(sc, st, true);
+    flush_lane_stats<RECHECK>(sc, st, true);
+}
+
+// FP64 recheck of the queued samples of the FP32 trace: each is classified in
+// FP64 at the FP32 trace's own position (its t, exact in double) on the FP64
+// ray.  The pixel is re-traced in FP64 when the escape count or the stop
+// decision differs, or when the FP64 values lie close enough to a threshold
+// (modulus within a tenth of the margin, estimate within half the band) that
+// the FP32 trace's rounding of its positions could move the FP64 trace's
+// decision.
+template <int SQ, int MOD>
+__global__ void __launch_bounds__(kBlock) de_recheck_kernel(const __grid_constant__ FrameDesc fd, const Scratch sc)
+{
+    const FrameT<double> &F = fd.d;
+    const unsigned nq = min(*(volatile unsigned *)&sc.ctr->queue_count, sc.queue_cap);
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += gridDim.x * blockDim.x) {
+        const int4 e = sc.queue[i];
+        const int pixel = e.x;
+        const int x = pixel % fd.W, y = pixel / fd.W;
+        double d[3], t_in, t_out, D[8];
+        camera_clip<double>(F, fd.W, fd.H, x, y, d, t_in, t_out);
+        slice_dir<double>(F, d, D);
+        const double t = (double)__int_as_float(e.z);
+        double z[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) z[j] = fma(t, D[j], F.A[j]);
+        double dist, dm;
+        const int n = classify_de<double, SQ, MOD, false>(z, F, fd.max_iter, true, dist, dm);
+        const bool stop = n == 0 || dist < F.de_eps;
+        const bool differs = n != (e.w & 0xffff) || stop != ((e.w >> 16) != 0);
+        const bool close = dm <= 0.1 * F.margin || (n != 0 && fabs(dist - F.de_eps) <= 0.5 * kDeEpsBand * F.de_eps);
+        if (differs || close) mark_dirty(fd, sc, pixel);
+    }
+}
+
+// FP64 re-trace of the pixels queued by the recheck, 32 per warp (one per
+// lane, in lockstep like de_kernel), shaded in place.
+template <int SQ, int MOD>
+__global__ void __launch_bounds__(kBlock) de_fixup_kernel(const __grid_constant__ FrameDesc fd, const Scratch sc)
+{
+    const FrameT<double> &F = fd.d;
+    const int lane = threadIdx.x & 31;
+    const unsigned nd = min(*(volatile unsigned *)&sc.ctr->dirty_count, sc.dirty_cap);
+    const unsigned warp = (threadIdx.x >> 5) * gridDim.x + blockIdx.x, nwarps = gridDim.x * (blockDim.x >> 5);
+    LaneStats st, st_fix;
+    for (unsigned base = warp * 32; base < nd; base += nwarps * 32) {
+        const bool valid = base + lane < nd;
+        const int pixel = valid ? sc.dirty_list[base + lane] : 0;
+        const int x = pixel % fd.W, y = pixel / fd.W;
+        double d[3], D[8], depth;
+        int n_star, esc_max;
+        const bool hit =
+            de_trace_lane<double, SQ, MOD, false, false>(fd, sc, x, y, valid, st_fix, d, D, depth, n_star, esc_max);
+        if (valid && !hit) write_miss<double>(fd, x, y, esc_max);
+        normal_shade<double, SQ, MOD>(fd, F, x, y, d, D, depth, n_star, hit, st_fix);
+        st.hits += valid ? 1 : 0;
+    }
+    flush_stat(&sc.ctr->stats[5], st.hits);
+    flush_stat(&sc.ctr->stats[6], st_fix.iters + st_fix.niters);
 }
 
 template <typename T, int SQ, int MOD>
@@ -180,11 +290,11 @@ __global__ void __launch_bounds__(kBlock) de_shade_kernel(const __grid_constant_
     flush_stat(&sc.ctr->stats[1], st.niters);
 }
 
-template <typename T, int SQ, int MOD>
+template <typename T, int SQ, int MOD, bool RECHECK>
 cudaError_t launch_de_t(const FrameDesc &fd, const Scratch &sc, cudaStream_t st, int num_sms, cudaEvent_t *ev)
 {
     static std::atomic<int> g_de{0}, g_sh{0};
-    const int cap_de = num_sms * resident_per_sm(g_de, de_kernel<T, SQ, MOD, false>);
+    const int cap_de = num_sms * resident_per_sm(g_de, de_kernel<T, SQ, MOD, false, RECHECK>);
     const int cap_sh = num_sms * resident_per_sm(g_sh, de_shade_kernel<T, SQ, MOD>);
     const unsigned ntiles = (unsigned)((fd.W + kDeTileW - 1) / kDeTileW) * (unsigned)((fd.H + kDeTileH - 1) / kDeTileH);
     const int gd = (int)min((unsigned)cap_de, (ntiles + 3u) / 4u);
@@ -192,13 +302,20 @@ cudaError_t launch_de_t(const FrameDesc &fd, const Scratch &sc, cudaStream_t st,
     const int gs = (int)min((unsigned)cap_sh, (maxw + 3u) / 4u);
     if (ev) cudaEventRecord(ev[0], st);
     if (fd.axis_slice)
-        de_kernel<T, SQ, MOD, true><<<gd > 0 ? gd : 1, kBlock, 0, st>>>(fd, sc);
+        de_kernel<T, SQ, MOD, true, RECHECK><<<gd > 0 ? gd : 1, kBlock, 0, st>>>(fd, sc);
     else
-        de_kernel<T, SQ, MOD, false><<<gd > 0 ? gd : 1, kBlock, 0, st>>>(fd, sc);
+        de_kernel<T, SQ, MOD, false, RECHECK><<<gd > 0 ? gd : 1, kBlock, 0, st>>>(fd, sc);
     if (ev) cudaEventRecord(ev[1], st);
     de_shade_kernel<T, SQ, MOD><<<gs > 0 ? gs : 1, kBlock, 0, st>>>(fd, sc);
-    if (ev) {
-        cudaEventRecord(ev[2], st);
+    if (ev) cudaEventRecord(ev[2], st);
+    if constexpr (RECHECK) {
+        static std::atomic<int> g_re{0}, g_fx{0};
+        de_recheck_kernel<SQ, MOD><<<num_sms * resident_per_sm(g_re, de_recheck_kernel<SQ, MOD>), kBlock, 0, st>>>(
+            fd, sc);
+        if (ev) cudaEventRecord(ev[3], st);
+        de_fixup_kernel<SQ, MOD><<<num_sms * resident_per_sm(g_fx, de_fixup_kernel<SQ, MOD>), kBlock, 0, st>>>(fd, sc);
+        if (ev) cudaEventRecord(ev[4], st);
+    } else if (ev) {
         cudaEventRecord(ev[3], st);
         cudaEventRecord(ev[4], st);
     }
@@ -208,8 +325,11 @@ cudaError_t launch_de_t(const FrameDesc &fd, const Scratch &sc, cudaStream_t st,
 template <int SQ, int MOD>
 cudaError_t launch_de_m(const FrameDesc &fd, const Scratch &sc, cudaStream_t st, int num_sms, cudaEvent_t *ev)
 {
-    return fd.precision == DQJ_FP64 ? launch_de_t<double, SQ, MOD>(fd, sc, st, num_sms, ev)
-                                    : launch_de_t<float, SQ, MOD>(fd, sc, st, num_sms, ev);
+    switch (fd.precision) {
+    case DQJ_FP64: return launch_de_t<double, SQ, MOD, false>(fd, sc, st, num_sms, ev);
+    case DQJ_FP32_RECHECK: return launch_de_t<float, SQ, MOD, true>(fd, sc, st, num_sms, ev);
+    default: return launch_de_t<float, SQ, MOD, false>(fd, sc, st, num_sms, ev);
+    }
 }
 
 }  // namespace

@@ -122,8 +122,6 @@ dqj_status validate(const dqj_params *p)
     if (p->traversal != DQJ_TRAVERSAL_MARCH && p->traversal != DQJ_TRAVERSAL_DE)
         return fail(DQJ_ERR_INVALID, "traversal must be DQJ_TRAVERSAL_MARCH or DQJ_TRAVERSAL_DE");
     if (p->traversal == DQJ_TRAVERSAL_DE) {
-        if (p->precision == DQJ_FP32_RECHECK)
-            return fail(DQJ_ERR_INVALID, "DQJ_TRAVERSAL_DE supports DQJ_FP32 and DQJ_FP64 only");
         if (p->de_max_steps < 1 || p->de_max_steps > 1000000)
             return fail(DQJ_ERR_INVALID, "de_max_steps must be in 1..1000000");
         if (!(p->de_epsilon > 0.0 && p->de_epsilon < 1e30)) return fail(DQJ_ERR_INVALID, "de_epsilon must be > 0");

@@ -149,11 +149,10 @@ def test_de_validation_rejects(lib, field, value):
     assert field.split("_")[0] in binding.last_error()
 
 
-def test_de_rejects_recheck_precision(lib):
-    p = binding.make_params(scenes.default_scene(traversal=scenes.TRAVERSAL_DE,
-                                                 precision=scenes.PRECISION_FP32_RECHECK))
-    assert lib.dqj_validate_params(binding.ctypes.byref(p)) == binding.DQJ_ERR_INVALID
-    assert "DQJ_TRAVERSAL_DE" in binding.last_error()
+def test_de_accepts_every_precision(lib):
+    for prec in (scenes.PRECISION_FP32, scenes.PRECISION_FP32_RECHECK, scenes.PRECISION_FP64):
+        p = binding.make_params(scenes.default_scene(traversal=scenes.TRAVERSAL_DE, precision=prec))
+        assert lib.dqj_validate_params(binding.ctypes.byref(p)) == binding.DQJ_OK
 
 
 def test_render_host_batch_argument_errors():

@@ -1,11 +1,14 @@
 """Distance-estimate sphere tracing (the paper's own traversal, Eq. distfract2)
 on the GPU against the FP64 oracle.
 
-FP64 is held to the render's full parity contract.  FP32 accumulates the ray
-parameter in single precision, so a sample whose estimate lies within rounding
-of epsilon can stop one step earlier or later: its hit/miss class and the
-contract hold on all but a few pixels, and the depth on >= 99 % of common hits
-(the step moves it by up to one estimate, below epsilon)."""
+FP64 and FP32 with the FP64 recheck are held to the render's full parity
+contract.  Plain FP32 is outside it: it accumulates the ray parameter in
+single precision, so a sample whose estimate lies within rounding of epsilon
+can stop one step earlier or later; its hit/miss class and the contract hold
+on all but a few pixels, and the depth on >= 99 % of common hits (the step
+moves it by up to one estimate, below epsilon).  The recheck mode re-evaluates
+such samples (and those whose escape test came within the margin of R^2) in
+FP64 and re-traces in FP64 the pixels whose decisions could differ."""
 import numpy as np
 import pytest
 
@@ -71,6 +74,9 @@ def test_de_against_oracle(rdr, name):
     st = binding.stats_dict(out["stats"])
     assert st["hits"] == int(np.isfinite(g32["depth"]).sum())
     assert st["samples"] >= st["hits"]
+    out_rc = rdr.render(dict(s, precision=scenes.PRECISION_FP32_RECHECK))
+    g_rc = to_numpy(out_rc, s["width"], s["height"])
+    assert_parity(compare(g_rc, o), what=f"DE FP32+recheck {name}")
 
 
 def test_de_full_hd_sampled(rdr):
@@ -85,6 +91,20 @@ def test_de_full_hd_sampled(rdr):
     st = binding.stats_dict(out["stats"])
     # sphere tracing takes far fewer samples than the 513-sample march
     assert st["samples"] < 40 * 1920 * 1080
+
+
+def test_de_full_hd_recheck_meets_contract(rdr):
+    # the default c at 1080p (many hits), every pixel, FP32 + FP64 recheck
+    s = de(width=1920, height=1080, max_iter=16, precision=scenes.PRECISION_FP32_RECHECK)
+    out = rdr.render(s)
+    g = to_numpy(out, 1920, 1080)
+    rep = compare(g, oracle.render(s))
+    assert_parity(rep, what="DE 1080p FP32+recheck, whole frame")
+    st = binding.stats_dict(out["stats"])
+    # every hit is re-traced in FP64, and the misses with a decision close to
+    # a threshold: a small fraction of the frame
+    hits = int(np.isfinite(g["depth"]).sum())
+    assert st["rechecks"] > 0 and hits <= st["fixups"] < hits + 0.01 * 1920 * 1080, st
 
 
 def test_de_noalloc_equals_render(rdr):
