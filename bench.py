@@ -455,6 +455,78 @@ def run_gpu(args, world, rank, local):
 
 
 
+def run_split(args, world, rank, local):
+    """The frame split across ranks (one GPU each): every rank renders the
+    tiles t with t mod N == rank of the five workload frames
+    (dqj_render_tiles), the output planes are gathered to every rank
+    (all_gather) and put together by tile owner, all inside the timed region.
+    Strong scaling: the whole frames' DQ iterations over the max-over-ranks
+    time."""
+    import torch
+
+    from paper_2303_14827_gb300 import binding
+    torch.cuda.set_device(local)
+    binding.load()
+    frames = workload_scenes(args.precision)
+    nf = len(frames)
+    W, H = frames[0]["width"], frames[0]["height"]
+    dev = f"cuda:{local}"
+    ctx = binding.dqj_create(local)
+    outs = [binding.alloc_outputs(W, H, device=dev) for _ in frames]
+    owners = [torch.as_tensor(binding.tile_parts_of_pixels(ctx, s, world), device=dev) for s in frames]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(local)
+    planes = ("iter", "depth", "normal", "rgba")
+    gath = {k: torch.empty((world,) + tuple(outs[0][k].shape), dtype=outs[0][k].dtype, device=dev) for k in planes}
+    if world > 1:
+        import torch.distributed as dist
+
+    def step(i):
+        flush.fill_(i & 0xFF)
+        for s, o, own in zip(frames, outs, owners):
+            binding.dqj_render_tiles(ctx, s, binding.outputs_of(o), stream.cuda_stream, rank, world)
+            if world > 1:  # gather every part, put each pixel from its tile's owner
+                for k in planes:
+                    dist.all_gather_into_tensor(gath[k], o[k])
+                    m = own[(...,) + (None,) * (o[k].dim() - 2)]
+                    o[k].copy_(torch.gather(gath[k], 0, m.expand_as(o[k]).unsqueeze(0)).squeeze(0))
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    barrier(world)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for i in range(args.steps):
+            step(args.warmup + i)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    ms = max_over_ranks(e0.elapsed_time(e1), world)
+    ctx2 = binding.dqj_create(local)  # the whole frames' algorithmic iterations
+    it = 0
+    for s, o in zip(frames, outs):
+        ref = binding.alloc_outputs(W, H, device=dev)
+        binding.dqj_render(ctx2, s, binding.outputs_of(ref), stream.cuda_stream)
+        torch.cuda.synchronize()
+        st = binding.stats_dict(ref["stats"])
+        it += st["class_iters"] + st["normal_iters"]
+    binding.dqj_destroy(ctx2)
+    binding.dqj_destroy(ctx)
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": it * args.steps / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": DTYPES[args.precision], "data": "synthetic",
+            "config": {"workload": WORKLOAD + ", " + MODE_NAMES[args.precision], "frames_per_step": nf,
+                       "l2": "256 MiB buffer written between steps", "parallelism": f"frame split x{world}",
+                       "gather": "all_gather of the output planes, put together by tile owner, in the timed region"},
+            "frames_per_s": nf * args.steps / (ms * 1e-3), "clocks": clk.summary(),
+            "gpu_launches": (4 if args.precision == 1 else 2) * nf * args.steps}), flush=True)
+    return 0
+
+
 # ---------------------------------------------------------------------------
 # served form: saturation, Poisson latency, and the mixed 64-frame batch
 # ---------------------------------------------------------------------------
@@ -1019,6 +1091,8 @@ def main():
     ap.add_argument("--precision", type=int, default=1, choices=(0, 1, 2),
                     help="headline mode: 0 FP32, 1 FP32 + FP64 recheck (default), 2 FP64")
     ap.add_argument("--no-precision-report", action="store_true")
+    ap.add_argument("--split", action="store_true",
+                    help="frame split across the ranks (tile subsets + gather, strong scaling) instead of replicas")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -1047,6 +1121,8 @@ def main():
         rc = run_voxel_only(args, world, rank, local)
     elif args.de:
         rc = run_de_only(args, world, rank, local)
+    elif args.split:
+        rc = run_split(args, world, rank, local)
     else:
         rc = run_gpu(args, world, rank, local)
     if world > 1:

@@ -218,6 +218,19 @@ dqj_status dqj_create(const dqj_config *cfg, dqj_ctx **out);
  * destroyed before the context (they use its events and scratch memory). */
 dqj_status dqj_render(dqj_ctx *ctx, const dqj_params *p, const dqj_outputs *out, void *cuda_stream);
 
+/* Frame split (several GPUs, one process each): render only the tiles t of
+ * the frame with t mod parts == part, writing their pixels' outputs and
+ * leaving every other pixel of the planes untouched.  Tile t covers the pixels
+ * with (y / th) * ceil(width / tw) + x / tw == t, where (tw, th) is
+ * dqj_tile_shape's tile for the march and 8 x 4 for DQJ_TRAVERSAL_DE.  The
+ * parts' planes put together (each pixel from the part that owns its tile)
+ * equal dqj_render's exactly: every pixel's arithmetic is its own.  part = 0,
+ * parts = 1 is dqj_render.  DQJ_ERR_INVALID unless 0 <= part < parts <= 65536.
+ * Stats count the part's own work.  An interface of this library (the frame
+ * split across GPUs); the paper has no counterpart. */
+dqj_status dqj_render_tiles(dqj_ctx *ctx, const dqj_params *p, const dqj_outputs *out, void *cuda_stream,
+                            int32_t part, int32_t parts);
+
 /* Render one frame into HOST buffers: the library renders into context-owned
  * device planes, copies the requested planes to the host and waits.  Blocking. */
 dqj_status dqj_render_host(dqj_ctx *ctx, const dqj_params *p, const dqj_outputs *host_out);

@@ -121,6 +121,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         L.dqj_validate_params.argtypes = [P(dqj_params)]
         L.dqj_create.argtypes = [P(dqj_config), P(ctypes.c_void_p)]
         L.dqj_render.argtypes = [ctypes.c_void_p, P(dqj_params), P(dqj_outputs), ctypes.c_void_p]
+        L.dqj_render_tiles.argtypes = [ctypes.c_void_p, P(dqj_params), P(dqj_outputs), ctypes.c_void_p,
+                                       ctypes.c_int32, ctypes.c_int32]
         L.dqj_render_host.argtypes = [ctypes.c_void_p, P(dqj_params), P(dqj_outputs)]
         L.dqj_render_host_batch.argtypes = [ctypes.c_void_p, P(dqj_params), P(dqj_outputs), ctypes.c_int32]
         L.dqj_submit.argtypes = [ctypes.c_void_p, P(dqj_params), P(dqj_outputs), P(ctypes.c_uint64)]
@@ -240,6 +242,27 @@ def dqj_render(ctx: int, scene: dict, outputs: dqj_outputs, stream: int = 0) -> 
     p = make_params(scene)
     check(load().dqj_render(ctypes.c_void_p(ctx), ctypes.byref(p), ctypes.byref(outputs),
                             ctypes.c_void_p(stream)))
+
+
+def dqj_render_tiles(ctx: int, scene: dict, outputs: dqj_outputs, stream: int, part: int, parts: int) -> None:
+    """Enqueue the frame's tiles t with t mod parts == part (the frame split)."""
+    p = make_params(scene)
+    check(load().dqj_render_tiles(ctypes.c_void_p(ctx), ctypes.byref(p), ctypes.byref(outputs),
+                                  ctypes.c_void_p(stream), part, parts))
+
+
+def tile_parts_of_pixels(ctx: int, scene: dict, parts: int):
+    """(height, width) int array: the part of dqj_render_tiles that renders each
+    pixel (its tile index mod parts), for putting the parts' planes together."""
+    import numpy as np
+    if scene.get("traversal", 0) == 1:
+        tw, th = 8, 4
+    else:
+        _, tw, th = dqj_tile_shape(ctx, scene)
+    w, h = scene["width"], scene["height"]
+    tiles_x = (w + tw - 1) // tw
+    ys, xs = np.meshgrid(np.arange(h), np.arange(w), indexing="ij")
+    return ((ys // th) * tiles_x + xs // tw) % parts
 
 
 def dqj_render_host(ctx: int, scene: dict, outputs: dqj_outputs) -> None:

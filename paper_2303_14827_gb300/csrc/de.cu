@@ -171,13 +171,14 @@ __global__ void __launch_bounds__(kBlock) de_kernel(const __grid_constant__ Fram
 {
     const int lane = threadIdx.x & 31;
     const int tiles_x = (fd.W + kDeTileW - 1) / kDeTileW;
-    const unsigned ntiles = (unsigned)tiles_x * (unsigned)((fd.H + kDeTileH - 1) / kDeTileH);
+    const unsigned ntiles = subset_tiles(fd, (unsigned)tiles_x * (unsigned)((fd.H + kDeTileH - 1) / kDeTileH));
     LaneStats st;
     for (;;) {
         unsigned tile = 0;
         if (lane == 0) tile = atomicAdd(&sc.ctr->tile_next, 1u);
         tile = __shfl_sync(kFull, tile, 0);
         if (tile >= ntiles) break;
+        tile = subset_tile(fd, tile);
         const int x = (int)(tile % (unsigned)tiles_x) * kDeTileW + lane % kDeTileW;
         const int y = (int)(tile / (unsigned)tiles_x) * kDeTileH + lane / kDeTileW;
         const bool valid = x < fd.W && y < fd.H;
@@ -296,7 +297,8 @@ cudaError_t launch_de_t(const FrameDesc &fd, const Scratch &sc, cudaStream_t st,
     static std::atomic<int> g_de{0}, g_sh{0};
     const int cap_de = num_sms * resident_per_sm(g_de, de_kernel<T, SQ, MOD, false, RECHECK>);
     const int cap_sh = num_sms * resident_per_sm(g_sh, de_shade_kernel<T, SQ, MOD>);
-    const unsigned ntiles = (unsigned)((fd.W + kDeTileW - 1) / kDeTileW) * (unsigned)((fd.H + kDeTileH - 1) / kDeTileH);
+    const unsigned ntiles =
+        subset_tiles(fd, (unsigned)((fd.W + kDeTileW - 1) / kDeTileW) * (unsigned)((fd.H + kDeTileH - 1) / kDeTileH));
     const int gd = (int)min((unsigned)cap_de, (ntiles + 3u) / 4u);
     const unsigned maxw = ((unsigned)fd.W * (unsigned)fd.H + 31u) / 32u;
     const int gs = (int)min((unsigned)cap_sh, (maxw + 3u) / 4u);

@@ -77,6 +77,8 @@ struct alignas(16) FrameDesc {
     uint32_t axis_slice;  // 1: slice origin and basis are zero in components 3..7
     int32_t k_split;      // march samples split into this many ranges across warps (1: not split)
     int32_t k_chunk;      // samples per range
+    int32_t tile_part;    // the frame's tiles t with t mod tile_parts == tile_part are rendered
+    int32_t tile_parts;   // (1: every tile)
 };
 
 // Counters at the head of the scratch block; zeroed before every frame.

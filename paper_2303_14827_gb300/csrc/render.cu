@@ -37,13 +37,14 @@ __global__ void __launch_bounds__(kBlock) march_kernel(const __grid_constant__ F
 {
     const FrameT<T> &F = frame<T>(fd);
     const int lane = threadIdx.x & 31;
-    const unsigned ntiles = (unsigned)fd.tiles_x * (unsigned)fd.tiles_y;
+    const unsigned ntiles = subset_tiles(fd, (unsigned)fd.tiles_x * (unsigned)fd.tiles_y);
     unsigned long long s_iters = 0, s_samples = 0, s_hits = 0, s_rechecks = 0;
     for (;;) {
         unsigned tile = 0;
         if (lane == 0) tile = atomicAdd(&sc.ctr->tile_next, 1u);
         tile = __shfl_sync(kFull, tile, 0);
         if (tile >= ntiles) break;
+        tile = subset_tile(fd, tile);
         const int tx = (int)(tile % (unsigned)fd.tiles_x), ty = (int)(tile / (unsigned)fd.tiles_x);
         const int x = tx * fd.tile_w + lane % fd.tile_w;
         const int y = ty * fd.tile_h + lane / fd.tile_w;
@@ -128,12 +129,13 @@ __global__ void __launch_bounds__(kBlock, AXIS ? 5 : 4)  // the general form kee
 {
     __shared__ int4 stage[RECHECK ? kBlock / 32 : 1][RECHECK ? kQStage : 1];  // recheck entries, per warp
     const int lane = threadIdx.x & 31;
-    const unsigned ntiles = (unsigned)fd.tiles_x * (unsigned)fd.tiles_y;
+    const unsigned ntiles = subset_tiles(fd, (unsigned)fd.tiles_x * (unsigned)fd.tiles_y);
     for (;;) {
         unsigned tile = 0;
         if (lane == 0) tile = atomicAdd(&sc.ctr->tile_next, 1u);
         tile = __shfl_sync(kFull, tile, 0);
         if (tile >= ntiles) break;
+        tile = subset_tile(fd, tile);
         // counters are added per tile, so none stays live across the march loop
         LaneStats st;
         march2_tile<SQ, MOD, RECHECK, AXIS>(fd, fd.p2, sc, tile, st, stage[RECHECK ? threadIdx.x >> 5 : 0]);
@@ -154,15 +156,15 @@ template <int SQ, int MOD, bool AXIS>
 __global__ void __launch_bounds__(kBlock, AXIS ? 5 : 4) march2_split_kernel(const __grid_constant__ FrameDesc fd, const Scratch sc)
 {
     const int lane = threadIdx.x & 31;
-    const unsigned items = (unsigned)fd.tiles_x * (unsigned)fd.tiles_y * (unsigned)fd.k_split;
+    const unsigned ntiles = subset_tiles(fd, (unsigned)fd.tiles_x * (unsigned)fd.tiles_y);
+    const unsigned items = ntiles * (unsigned)fd.k_split;
     for (;;) {
         unsigned item = 0;
         if (lane == 0) item = atomicAdd(&sc.ctr->tile_next, 1u);
         item = __shfl_sync(kFull, item, 0);
         if (item >= items) break;
         // lower ranges first, so that later ones find the rays they can skip
-        const unsigned ntiles = (unsigned)fd.tiles_x * (unsigned)fd.tiles_y;
-        const unsigned r = item / ntiles, tile = item % ntiles;
+        const unsigned r = item / ntiles, tile = subset_tile(fd, item % ntiles);
         const int kb = (int)r * fd.k_chunk, ke = min(kb + fd.k_chunk, fd.N + 1);
         LaneStats st;
         march2_tile<SQ, MOD, false, AXIS, true>(fd, fd.p2, sc, tile, st, nullptr, kb, ke);
@@ -179,7 +181,10 @@ __global__ void __launch_bounds__(kBlock) march_merge_kernel(const __grid_consta
     LaneStats st;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < npx; base += (int64_t)gridDim.x * blockDim.x) {
         const int64_t pixel = base + threadIdx.x;
-        const bool part = pixel < npx;
+        const int x = (int)(pixel % fd.W), y = (int)(pixel / fd.W);
+        // only the pixels of the frame's tile subset (dqj_render_tiles)
+        const unsigned tile = (unsigned)(y / fd.tile_h) * (unsigned)fd.tiles_x + (unsigned)(x / fd.tile_w);
+        const bool part = pixel < npx && tile % (unsigned)fd.tile_parts == (unsigned)fd.tile_part;
         int kf = -1, m = 0;
         unsigned iters = 0, samples = 0;
         for (int r = 0; part && r < fd.k_split; ++r) {
@@ -196,7 +201,6 @@ __global__ void __launch_bounds__(kBlock) march_merge_kernel(const __grid_consta
         st.iters += iters;
         st.samples += samples;
         st.hits += hit ? 1 : 0;
-        const int x = (int)(pixel % fd.W), y = (int)(pixel / fd.W);
         if (part && !hit) write_miss<float>(fd, x, y, m);
         warp_push(hit, make_int4((int)pixel, kf, 0, 0), sc.hits, sc.hit_cap, &sc.ctr->hit_count);
     }
@@ -257,7 +261,7 @@ template <typename T, int SQ, int MOD, bool RECHECK>
 cudaError_t launch_passes(const FrameDesc &fd, const Scratch &sc, cudaStream_t st, int num_sms, cudaEvent_t *ev)
 {
     static std::atomic<int> g_march{0}, g_march2a{0}, g_march2g{0}, g_bisect{0};
-    const unsigned ntiles = (unsigned)fd.tiles_x * (unsigned)fd.tiles_y;
+    const unsigned ntiles = subset_tiles(fd, (unsigned)fd.tiles_x * (unsigned)fd.tiles_y);
     if (ev) cudaEventRecord(ev[0], st);
     if constexpr (sizeof(T) == 4 && !RECHECK) {
         if (fd.march_variant == 1 && fd.k_split > 1) {
@@ -336,8 +340,8 @@ int march_split(const FrameDesc &fd, int num_sms)
         return (int)std::min<long>(std::min<long>(n, 64), (long)fd.N + 1);
     }
     const long long warps = (long long)num_sms * resident_per_sm(g_occ, march2_split_kernel<0, 0, true>) * (kBlock / 32);
-    const long long tiles = (long long)fd.tiles_x * fd.tiles_y;
-    if (tiles >= warps) return 1;
+    const long long tiles = subset_tiles(fd, (unsigned)fd.tiles_x * (unsigned)fd.tiles_y);
+    if (tiles >= warps || tiles == 0) return 1;
     // about four waves of items: later waves skip the rays earlier ranges hit
     const long long p = (4 * warps + tiles - 1) / tiles;
     return (int)std::min<long long>(std::min<long long>(p, 16), (long long)fd.N + 1);

@@ -31,6 +31,18 @@ inline int resident_per_sm(std::atomic<int> &slot, K kernel)
     return v;
 }
 
+// The frame's tile subset (dqj_render_tiles): the number of its tiles out of
+// ntiles, and the tile index of the subset's i-th tile.
+__host__ __device__ __forceinline__ unsigned subset_tiles(const FrameDesc &fd, unsigned ntiles)
+{
+    const unsigned part = (unsigned)fd.tile_part, parts = (unsigned)fd.tile_parts;
+    return part < ntiles ? (ntiles - part + parts - 1) / parts : 0u;
+}
+__device__ __forceinline__ unsigned subset_tile(const FrameDesc &fd, unsigned i)
+{
+    return i * (unsigned)fd.tile_parts + (unsigned)fd.tile_part;
+}
+
 // Per-lane counters, added to the frame's stats once per warp (DQJ_STAT_*).
 struct LaneStats {
     unsigned long long iters = 0, samples = 0, hits = 0, rechecks = 0, niters = 0;

@@ -295,6 +295,8 @@ void derive_frame(const dqj_params &p, FrameDesc &fd, int tile_w, int tile_h)
     fd.tiles_y = (p.height + tile_h - 1) / tile_h;
     fd.k_split = 1;
     fd.k_chunk = fd.N + 1;
+    fd.tile_part = 0;
+    fd.tile_parts = 1;
 }
 
 static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -395,14 +397,18 @@ void pick_tile_shape(dqj_ctx *ctx, const dqj_params &p, int &variant, int &tw, i
     }
 }
 
-// Enqueue the passes of one frame; ctx->mu held.
-static dqj_status enqueue_frame(dqj_ctx *ctx, const dqj_params &p, const dqj_outputs &out, cudaStream_t st)
+// Enqueue the passes of one frame (of its tiles t with t mod parts == part);
+// ctx->mu held.
+static dqj_status enqueue_frame(dqj_ctx *ctx, const dqj_params &p, const dqj_outputs &out, cudaStream_t st,
+                                int part = 0, int parts = 1)
 {
     int variant, tw, th;
     pick_tile_shape(ctx, p, variant, tw, th);
     FrameDesc fd;
     derive_frame(p, fd, tw, th);
     fd.march_variant = variant;
+    fd.tile_part = part;
+    fd.tile_parts = parts;
     fd.pitch = out.pitch_px;
     fd.iter = out.iter;
     fd.depth = out.depth;
@@ -426,12 +432,13 @@ static dqj_status enqueue_frame(dqj_ctx *ctx, const dqj_params &p, const dqj_out
     fd.k_split = march_split(fd, ctx->num_sms);
     fd.k_chunk = (fd.N + 1 + fd.k_split - 1) / fd.k_split;
     fd.k_split = (fd.N + 1 + fd.k_chunk - 1) / fd.k_chunk;  // every range holds a sample
-    const uint64_t part = fd.k_split > 1 ? (uint64_t)fd.k_split * px : 0;
+    const uint64_t part_entries = fd.k_split > 1 ? (uint64_t)fd.k_split * px : 0;
     ScratchBuf &sb = ctx->scratch;
-    if (capturing && !(sb.base && px <= sb.pixels && (!recheck || sb.with_queue) && part <= sb.part_entries))
+    if (capturing &&
+        !(sb.base && px <= sb.pixels && (!recheck || sb.with_queue) && part_entries <= sb.part_entries))
         return fail(DQJ_ERR_INVALID, "render: under stream capture the context's scratch must already fit the frame "
                                      "(render the largest frame once before capturing)");
-    dqj_status s = scratch_ensure(sb, px, recheck, part);
+    dqj_status s = scratch_ensure(sb, px, recheck, part_entries);
     if (s != DQJ_OK) return s;
     if (capturing) {
         if (recheck) {
@@ -488,17 +495,25 @@ dqj_status check_outputs(const dqj_params &p, const dqj_outputs *out)
     return DQJ_OK;
 }
 
-dqj_status render_on_stream(dqj_ctx *ctx, const dqj_params *p, const dqj_outputs *out, cudaStream_t st)
+dqj_status render_on_stream(dqj_ctx *ctx, const dqj_params *p, const dqj_outputs *out, cudaStream_t st, int part,
+                            int parts)
 {
     dqj_status s = validate(p);
     if (s != DQJ_OK) return s;
     s = check_outputs(*p, out);
     if (s != DQJ_OK) return s;
+    if (parts < 1 || parts > 65536 || part < 0 || part >= parts)
+        return fail(DQJ_ERR_INVALID, "tile parts must satisfy 0 <= part < parts <= 65536");
     if (ctx->device == DQJ_DEVICE_MOCK) return fail(DQJ_ERR_INVALID, "a mock context cannot render");
     std::lock_guard<std::mutex> lk(ctx->mu);
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_fail(e, "render: cudaSetDevice");
-    return enqueue_frame(ctx, *p, *out, st);
+    return enqueue_frame(ctx, *p, *out, st, part, parts);
+}
+
+dqj_status render_on_stream(dqj_ctx *ctx, const dqj_params *p, const dqj_outputs *out, cudaStream_t st)
+{
+    return render_on_stream(ctx, p, out, st, 0, 1);
 }
 
 }  // namespace dqj
@@ -607,6 +622,15 @@ dqj_status dqj_render(dqj_ctx *ctx, const dqj_params *p, const dqj_outputs *out,
     return dqj::guarded([&]() -> dqj_status {
         if (!ctx) return fail(DQJ_ERR_INVALID, "ctx is NULL");
         return render_on_stream(ctx, p, out, static_cast<cudaStream_t>(cuda_stream));
+    });
+}
+
+dqj_status dqj_render_tiles(dqj_ctx *ctx, const dqj_params *p, const dqj_outputs *out, void *cuda_stream,
+                            int32_t part, int32_t parts)
+{
+    return dqj::guarded([&]() -> dqj_status {
+        if (!ctx) return fail(DQJ_ERR_INVALID, "ctx is NULL");
+        return render_on_stream(ctx, p, out, static_cast<cudaStream_t>(cuda_stream), part, parts);
     });
 }
 

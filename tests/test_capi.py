@@ -195,3 +195,32 @@ def test_tile_cache_parsing_on_a_mock_context(tmp_path):
         assert binding.dqj_tile_shape(ctx, scenes.default_scene(width=256, height=256)) == (1, 8, 8)
     finally:
         binding.dqj_destroy(ctx)
+
+
+def test_tile_parts_of_pixels_partition_the_frame():
+    """The owner map used to put dqj_render_tiles parts together: each pixel's
+    part is its tile index (8 x 8 march tiles on a mock context, 8 x 4 for the
+    distance-estimate traversal) mod the number of parts, so the parts cover
+    the frame once and a tile never straddles two parts."""
+    import numpy as np
+    ctx = binding.dqj_create(-1)
+    try:
+        for scene, (tw, th) in ((scenes.default_scene(width=37, height=29), (8, 8)),
+                                (scenes.default_scene(width=37, height=29, traversal=scenes.TRAVERSAL_DE), (8, 4))):
+            assert (binding.dqj_tile_shape(ctx, scene)[1:] == (8, 8)) or scene["traversal"] == 1
+            for parts in (1, 2, 3, 7):
+                own = binding.tile_parts_of_pixels(ctx, scene, parts)
+                assert own.shape == (29, 37) and own.min() >= 0 and own.max() < parts
+                tiles_x = -(-37 // tw)
+                for y in range(29):
+                    for x in range(37):
+                        assert own[y, x] == ((y // th) * tiles_x + x // tw) % parts
+                # synthetic parts, each holding its own pixels, put back together
+                whole = np.arange(29 * 37).reshape(29, 37)
+                planes = [np.where(own == r, whole, -1) for r in range(parts)]
+                put = planes[0].copy()
+                for r in range(1, parts):
+                    put[own == r] = planes[r][own == r]
+                assert np.array_equal(put, whole)
+    finally:
+        binding.dqj_destroy(ctx)
