@@ -455,6 +455,20 @@ def run_gpu(args, world, rank, local):
 
 
 
+def gather_parts(planes, gathered, owner, world):
+    """The gather of the frame split: every rank's output planes (dict of
+    (H, pitch, ...) tensors, each rank's own tiles rendered) are all-gathered
+    into `gathered` (dict of (world, H, pitch, ...) tensors), and each pixel is
+    taken from the rank that owns its tile (`owner`, (H, pitch) int64)."""
+    import torch
+    import torch.distributed as dist
+    for k, o in planes.items():
+        g = gathered[k]
+        dist.all_gather_into_tensor(g.view((-1,) + tuple(g.shape[2:])), o.contiguous())  # parts along dim 0
+        m = owner[(...,) + (None,) * (o.dim() - 2)]
+        o.copy_(torch.gather(gathered[k], 0, m.expand_as(o).unsqueeze(0)).squeeze(0))
+
+
 def run_split(args, world, rank, local):
     """The frame split across ranks (one GPU each): every rank renders the
     tiles t with t mod N == rank of the five workload frames
@@ -478,18 +492,12 @@ def run_split(args, world, rank, local):
     stream = torch.cuda.current_stream(local)
     planes = ("iter", "depth", "normal", "rgba")
     gath = {k: torch.empty((world,) + tuple(outs[0][k].shape), dtype=outs[0][k].dtype, device=dev) for k in planes}
-    if world > 1:
-        import torch.distributed as dist
-
     def step(i):
         flush.fill_(i & 0xFF)
         for s, o, own in zip(frames, outs, owners):
             binding.dqj_render_tiles(ctx, s, binding.outputs_of(o), stream.cuda_stream, rank, world)
             if world > 1:  # gather every part, put each pixel from its tile's owner
-                for k in planes:
-                    dist.all_gather_into_tensor(gath[k], o[k])
-                    m = own[(...,) + (None,) * (o[k].dim() - 2)]
-                    o[k].copy_(torch.gather(gath[k], 0, m.expand_as(o[k]).unsqueeze(0)).squeeze(0))
+                gather_parts({k: o[k] for k in planes}, gath, own, world)
 
     for i in range(args.warmup):
         step(i)
