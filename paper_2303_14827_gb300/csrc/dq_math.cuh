@@ -201,6 +201,20 @@ __device__ __forceinline__ T dq_iter_axis_first(const T (&zi)[8], T (&z)[8], T &
     return x;
 }
 
+// classify_scalar for a sample of an axis-aligned slice (components 3..7 of z
+// zero): the first step takes dq_iter_axis_first, the same iterate as dq_iter
+// there.  Same return convention.
+template <typename T, int SQ, int MOD>
+__device__ __forceinline__ int classify_scalar_axis(T (&z)[8], const FrameT<T> &F, int max_iter)
+{
+    T sp = dfma(z[2], z[2], z[1] * z[1]);
+    if (max_iter < 1) return 0;
+    if (dq_iter_axis_first<T, MOD>(z, z, sp, F.c) > F.R2) return 1;
+    for (int n = 2; n <= max_iter; ++n)
+        if (dq_iter<T, SQ, MOD>(z, z, sp, F.c) > F.R2) return n;
+    return 0;
+}
+
 // classify_scalar that also reports whether any tested modulus, up to and
 // including the escaping one, lay within F.margin of R^2.
 template <typename T, int SQ, int MOD>

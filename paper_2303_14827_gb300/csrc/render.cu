@@ -210,18 +210,30 @@ __global__ void __launch_bounds__(kBlock) march_merge_kernel(const __grid_consta
 // ---------------------------------------------------------------------------
 // bisect + normal + shade over the hit list
 // ---------------------------------------------------------------------------
+// Hit lists shorter than group_below take group_lanes (4 or 8) lanes per hit
+// (bisect_group): one lane per hit would give the launch's warps too few hits
+// to hide the bisection's dependent chain.  Longer lists take one lane per hit
+// (the least work per hit).  All forms give the same results.
 template <typename T, int SQ, int MOD, bool RECHECK>
-__global__ void __launch_bounds__(kBlock) bisect_kernel(const __grid_constant__ FrameDesc fd, const Scratch sc)
+__global__ void __launch_bounds__(kBlock) bisect_kernel(const __grid_constant__ FrameDesc fd, const Scratch sc,
+                                                        unsigned group_below, int group_lanes)
 {
     const int lane = threadIdx.x & 31;
     const unsigned nhits = min(*(volatile unsigned *)&sc.ctr->hit_count, sc.hit_cap);
+    const int lanes = nhits < group_below ? group_lanes : 1;
+    const unsigned per = 32u / (unsigned)lanes;
     LaneStats st;
     for (;;) {
         unsigned base = 0;
-        if (lane == 0) base = atomicAdd(&sc.ctr->hit_next, 32u);
+        if (lane == 0) base = atomicAdd(&sc.ctr->hit_next, per);
         base = __shfl_sync(kFull, base, 0);
         if (base >= nhits) break;
-        bisect_chunk<T, SQ, MOD, RECHECK>(fd, sc, base, nhits, st);
+        if (lanes == 8)
+            bisect_group<T, SQ, MOD, RECHECK, 8>(fd, sc, base, nhits, st);
+        else if (lanes == 4)
+            bisect_group<T, SQ, MOD, RECHECK, 4>(fd, sc, base, nhits, st);
+        else
+            bisect_chunk<T, SQ, MOD, RECHECK>(fd, sc, base, nhits, st);
     }
     flush_lane_stats<RECHECK>(sc, st, false);
 }
@@ -255,6 +267,27 @@ __global__ void __launch_bounds__(kBlock) fixup_kernel(const __grid_constant__ F
         if (v) atomicAdd(&sc.ctr->stats[6], v);
         if (p) atomicAdd(&sc.ctr->stats[5], p);
     }
+}
+
+// Lanes per hit of a short hit list, and the hit-list length below which a
+// list counts as short: fewer hits than 32 per resident warp of the bisection
+// launch (capb CTAs of four warps).  DQJ_BISECT_GROUP = 1, 4 or 8 forces that
+// many lanes per hit for every list.
+int bisect_forced_lanes()
+{
+    static const int forced = [] {
+        const char *e = std::getenv("DQJ_BISECT_GROUP");
+        const long v = e ? std::strtol(e, nullptr, 10) : 0L;
+        return v == 1 || v == 4 || v == 8 ? (int)v : 0;
+    }();
+    return forced;
+}
+int bisect_group_lanes() { return bisect_forced_lanes() > 1 ? bisect_forced_lanes() : 4; }
+unsigned bisect_group_below(int capb)
+{
+    if (bisect_forced_lanes() == 1) return 0u;
+    if (bisect_forced_lanes() > 1) return 0xffffffffu;
+    return (unsigned)capb * 4u * 32u;
 }
 
 template <typename T, int SQ, int MOD, bool RECHECK>
@@ -303,7 +336,8 @@ cudaError_t launch_passes(const FrameDesc &fd, const Scratch &sc, cudaStream_t s
     const int capb = num_sms * resident_per_sm(g_bisect, bisect_kernel<T, SQ, MOD, RECHECK>);
     const unsigned maxw = ((unsigned)fd.W * (unsigned)fd.H + 31u) / 32u;
     const int gb = (int)min((unsigned)capb, (maxw + 3u) / 4u);
-    bisect_kernel<T, SQ, MOD, RECHECK><<<gb > 0 ? gb : 1, kBlock, 0, st>>>(fd, sc);
+    bisect_kernel<T, SQ, MOD, RECHECK><<<gb > 0 ? gb : 1, kBlock, 0, st>>>(fd, sc, bisect_group_below(capb),
+                                                                          bisect_group_lanes());
     if (ev) cudaEventRecord(ev[2], st);
     if (RECHECK) {
         static std::atomic<int> g_re{0}, g_fx{0};

@@ -13,17 +13,17 @@ namespace dqj {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kBlock = 128;  // 4 warps per CTA
 
-// Resident CTAs of `kernel` per SM at kBlock threads, cached in `slot` (one slot
+// Resident CTAs of `kernel` per SM at `block` threads, cached in `slot` (one slot
 // per kernel instantiation).  The count depends on the kernel's registers and
 // shared memory only, so it holds for every device of this single-architecture
 // build; callers multiply it by the launching device's SM count.  Threads that
 // race on an empty slot compute and store the same value.
 template <typename K>
-inline int resident_per_sm(std::atomic<int> &slot, K kernel)
+inline int resident_per_sm(std::atomic<int> &slot, K kernel, int block = kBlock)
 {
     int v = slot.load(std::memory_order_relaxed);
     if (v > 0) return v;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kernel, kBlock, 0) != cudaSuccess || v < 1) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kernel, block, 0) != cudaSuccess || v < 1) {
         cudaGetLastError();
         return 1;
     }
@@ -264,11 +264,25 @@ __device__ __forceinline__ void recheck_entry(const FrameDesc &fd, const Scratch
         t = lo + 0.5 * (hi - lo);
     }
     double z[8];
+    int n64;
+    if (fd.axis_slice) {
+        // components 3..7 of the slice point are zero (the general sum below
+        // gives +-0 there), so the first step takes the axis form, whose
+        // operations are those of dq_iter on those zeros: the same iterate
 #pragma unroll
-    for (int j = 0; j < 8; ++j)
-        z[j] = F.O[j] + (F.eye[0] + t * d[0]) * F.E[0][j] + (F.eye[1] + t * d[1]) * F.E[1][j] +
-               (F.eye[2] + t * d[2]) * F.E[2][j];
-    const int n64 = classify_scalar<double, SQ, MOD>(z, F, fd.max_iter);
+        for (int j = 0; j < 3; ++j)
+            z[j] = F.O[j] + (F.eye[0] + t * d[0]) * F.E[0][j] + (F.eye[1] + t * d[1]) * F.E[1][j] +
+                   (F.eye[2] + t * d[2]) * F.E[2][j];
+#pragma unroll
+        for (int j = 3; j < 8; ++j) z[j] = 0.0;
+        n64 = classify_scalar_axis<double, SQ, MOD>(z, F, fd.max_iter);
+    } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            z[j] = F.O[j] + (F.eye[0] + t * d[0]) * F.E[0][j] + (F.eye[1] + t * d[1]) * F.E[1][j] +
+                   (F.eye[2] + t * d[2]) * F.E[2][j];
+        n64 = classify_scalar<double, SQ, MOD>(z, F, fd.max_iter);
+    }
     if (n64 != e.w) mark_dirty(fd, sc, pixel);
 }
 
@@ -303,10 +317,16 @@ __device__ __forceinline__ void fixup_pixel(const FrameDesc &fd, int pixel, unsi
                 z[j] = F.O[j] + (F.eye[0] + t * d[0]) * F.E[0][j] + (F.eye[1] + t * d[1]) * F.E[1][j] +
                        (F.eye[2] + t * d[2]) * F.E[2][j];
         };
+        // FP64 classification; an axis-aligned slice takes the axis form of the
+        // first step (the same iterate, see classify_scalar_axis)
+        auto cls64 = [&](double (&z)[8]) {
+            return fd.axis_slice ? classify_scalar_axis<double, SQ, MOD>(z, F, fd.max_iter)
+                                 : classify_scalar<double, SQ, MOD>(z, F, fd.max_iter);
+        };
         auto cls = [&](double t) {
             double z[8];
             slice(t, z);
-            return classify_scalar<double, SQ, MOD>(z, F, fd.max_iter);
+            return cls64(z);
         };
         // a march sample: FP32 first, FP64 only when some FP32 modulus came within
         // the recheck margin of R^2 (the premise of the recheck mode: outside the
@@ -319,7 +339,7 @@ __device__ __forceinline__ void fixup_pixel(const FrameDesc &fd, int pixel, unsi
             for (int j = 0; j < 8; ++j) zf[j] = (float)z[j];
             bool marginal;
             const int n32 = classify_scalar_margin<float, SQ, MOD>(zf, fd.f, fd.max_iter, marginal);
-            return marginal ? classify_scalar<double, SQ, MOD>(z, F, fd.max_iter) : n32;
+            return marginal ? cls64(z) : n32;
         };
         int esc_max = 0, n_prev = 0, k_first = -1;
         for (int k0 = 0; k0 <= fd.N; k0 += 32) {
@@ -409,6 +429,14 @@ __device__ __forceinline__ void fixup_pixel(const FrameDesc &fd, int pixel, unsi
     } while (false);
 }
 
+// Device clock in nanoseconds, for the time limits of bounded waits.
+__device__ __forceinline__ unsigned long long globaltimer_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
 // Recheck entries of one warp are staged in shared memory.  At the end of its
 // tile the warp rechecks them itself in FP64 (recheck_staged): that FP64 work
 // overlaps with the FP32 march of the other warps on the SM instead of running
@@ -461,7 +489,8 @@ __device__ __forceinline__ void recheck_staged(const FrameDesc &fd, const Scratc
 
 // One 64-ray tile of the paired march (see march2_kernel); all 32 lanes call.
 // A lane holds tile slots `lane` and `lane + 32`.  RECHECK: qs is the warp's
-// staging buffer of kQStage entries in shared memory.  SPLIT: only samples
+// staging buffer of kQStage entries in shared memory, rechecked at the end of
+// the tile.  SPLIT: only samples
 // [kb, ke) of each ray, with the range's partial result written to sc.part
 // (range r = kb / fd.k_chunk) for march_merge_kernel instead of the outputs;
 // a ray for which a lower range has already found an inside sample is
@@ -739,6 +768,154 @@ __device__ __forceinline__ void bisect_chunk(const FrameDesc &fd, const Scratch 
     normal_shade<T, SQ, MOD>(fd, F, x, y, d, D, depth, n_lo, part, st);
     st.iters += iters;
     st.samples += samples;
+}
+
+// The same bisection, normal and shading for hit-list entries [base, base +
+// 32 / L) clipped to nhits, L lanes per hit (L = 4 or 8; lane group g = lane / L
+// takes entry base + g; all 32 lanes call).  For frames with few hits per SM,
+// where one lane per hit leaves the bisection's dependent chain of B + 7
+// classifications exposed: here the lanes of a group classify the midpoints of
+// log2(L) levels of the bisection tree at once (lane j < L - 1 holds node j + 1:
+// node 1 the next midpoint, children 2i inside -> [lo, mid] and 2i + 1 outside
+// -> [mid, hi]), each deriving its interval with the sequential halvings' own
+// operations, and the group replays the path; the six normal evaluations are
+// spread over the group's lanes.  Brackets, n*, depths, normals, queued
+// rechecks and the counted iterations (only the nodes on the path count) are
+// those of bisect_chunk.
+template <typename T, int SQ, int MOD, bool RECHECK, int L>
+__device__ __forceinline__ void bisect_group(const FrameDesc &fd, const Scratch &sc, unsigned base, unsigned nhits,
+                                             LaneStats &st)
+{
+    static_assert(L == 4 || L == 8, "four or eight lanes per hit");
+    constexpr int kLevels = L == 8 ? 3 : 2;  // tree levels per round
+    const FrameT<T> &F = frame<T>(fd);
+    const int lane = threadIdx.x & 31;
+    const int j = lane & (L - 1), gb = lane & ~(L - 1);  // lane in the group, the group's first lane
+    const unsigned idx = base + (unsigned)(lane / L);
+    const bool part = idx < nhits;
+    int4 e = make_int4(0, 0, 0, 0);
+    if (part) e = __ldcg(sc.hits + idx);  // L2: the list may be rewritten within one serving launch
+    const int pixel = e.x, k_first = e.y;
+    const int x = pixel % fd.W, y = pixel / fd.W;
+    T d[3] = {T(0), T(0), T(1)};
+    T t_in = T(0), t_out = T(0);
+    if (part) camera_clip<T>(F, fd.W, fd.H, x, y, d, t_in, t_out);
+    T D[8];
+    slice_dir<T>(F, d, D);
+    const T delta = (t_out - t_in) / T(fd.N);
+    const bool bis = part && k_first > 0;
+    T lo = bis ? dfma(T(k_first - 1), delta, t_in) : t_in;
+    T hi = bis ? dfma(T(k_first), delta, t_in) : t_in;
+    // n* starts as the escape count of march sample k_first - 1, classified
+    // again with the march's position and arithmetic (not counted): on the
+    // group's last lane, in the first round where that form is the midpoints'
+    // form, else (the FP32 march's first-iterate form of a general slice) before
+    int n_lo = fd.max_iter;
+    bool lo_in_round0 = true;
+    if constexpr (sizeof(T) == 4) {
+        if (!fd.axis_slice) {
+            lo_in_round0 = false;
+            T z[8];
+            float Q0[8], Q1[8], Q2[8], dot;
+            first_iterate_coeffs<float, SQ>(F.A, D, F.c, dot, Q0, Q1, Q2);
+            first_iterate<float, 8>(vfma((float)(k_first - 1), delta, vadd(t_in, dot)), Q0, Q1, Q2, z);
+            bool mg;
+            const int n = classify_lockstep_it1<T, SQ, MOD, false>(z, F, fd.max_iter, bis && j == L - 1, mg);
+            const int nl = __shfl_sync(kFull, n, gb + L - 1);
+            if (bis) n_lo = nl;
+        }
+    }
+    unsigned path = 0;
+    unsigned iters = 0, samples = 0, rechecks = 0;
+    const int node = j + 1, level = 31 - __clz(node);  // last lane: node L, level kLevels (no node)
+    for (int b0 = 0; b0 < fd.B || (b0 == 0 && lo_in_round0); b0 += kLevels) {
+        const int levels = min(kLevels, fd.B - b0);
+        const bool lo_lane = b0 == 0 && lo_in_round0 && j == L - 1;
+        T l = lo, h = hi;
+        for (int q = level - 1; q >= 0; --q) {  // path bits below the node's leading one
+            const T mid = l + T(0.5) * (h - l);
+            if ((node >> q) & 1)
+                l = mid;
+            else
+                h = mid;
+        }
+        const T pos = lo_lane ? lo : l + T(0.5) * (h - l);
+        const bool act = bis && (lo_lane || level < levels);
+        T z[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) z[i] = dfma(pos, D[i], F.A[i]);
+        bool mg;
+        const int n = classify_lockstep<T, SQ, MOD, RECHECK>(z, F, fd.max_iter, act, mg);
+        if (b0 == 0 && lo_in_round0) {
+            const int nl = __shfl_sync(kFull, n, gb + L - 1);
+            if (bis) n_lo = nl;
+        }
+        // replay the path through the levels of this round
+        int cur = 1;
+        for (int lv = 0; lv < kLevels; ++lv) {
+            const int nc = __shfl_sync(kFull, n, gb + cur - 1);
+            const bool mc = RECHECK ? __shfl_sync(kFull, mg, gb + cur - 1) : false;
+            if (lv >= levels) break;  // warp-uniform
+            const int b = b0 + lv;
+            if (RECHECK) {
+                const bool push = bis && mc && j == 0;
+                if (warp_push(push, make_int4(pixel, k_first | (b << 16), (int)path, nc), sc.queue, sc.queue_cap,
+                              &sc.ctr->queue_count)) {
+                    atomicAdd(&sc.ctr->stats[7], 1ull);
+                    mark_dirty(fd, sc, pixel);
+                }
+                rechecks += push ? 1 : 0;
+            }
+            const T mid = lo + T(0.5) * (hi - lo);
+            if (bis) {
+                iters += nc ? (unsigned)nc : (unsigned)fd.max_iter;
+                samples += 1;
+                if (nc == 0) {
+                    hi = mid;
+                } else {
+                    lo = mid;
+                    n_lo = nc;
+                    path |= 1u << b;
+                }
+            }
+            cur = 2 * cur + (nc != 0 ? 1 : 0);
+        }
+    }
+    const T depth = bis ? lo + T(0.5) * (hi - lo) : t_in;
+    // normal: evaluation q = 2a + s (F at depth -+ h e_a, s = 0: +h) runs on
+    // lane q mod L of the group, in round q / L
+    int nmax = part ? n_lo : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nmax = max(nmax, __shfl_xor_sync(kFull, nmax, o));
+    T fvq[6];
+    bool guard = false;
+#pragma unroll
+    for (int q0 = 0; q0 < 6; q0 += L) {
+        const int q = q0 + j;
+        const int a = q < 6 ? q >> 1 : 0;
+        const T hs = (q & 1) == 0 ? F.h : -F.h;
+        T z[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) z[i] = dfma(hs, F.E[a][i], dfma(depth, D[i], F.A[i]));
+        T sp = dq_sp<T>(z);
+        const int ns = part && q < 6 ? n_lo : 0;
+        for (int n = 0; n < nmax; ++n)
+            if (n < ns) dq_iter<T, SQ, MOD>(z, z, sp, F.c);
+        const T fv = modulus<T, MOD>(z);
+        const unsigned bad = __ballot_sync(kFull, q < 6 && !(fv <= normal_fmax(T(0))));
+        guard = guard || ((bad >> gb) & ((1u << L) - 1u)) != 0;
+#pragma unroll
+        for (int i = 0; i < L; ++i)
+            if (q0 + i < 6) fvq[q0 + i] = __shfl_sync(kFull, fv, gb + i);
+    }
+    if (part && j == 0) {
+        T g[3] = {fvq[0] - fvq[1], fvq[2] - fvq[3], fvq[4] - fvq[5]};
+        st.niters += 6ull * (unsigned)n_lo;
+        shade_write<T>(fd, F, x, y, n_lo, depth, g, guard, d);
+        st.iters += iters;
+        st.samples += samples;
+        if (RECHECK) st.rechecks += rechecks;
+    }
 }
 
 // Add a warp's lane counters to the frame's stats.

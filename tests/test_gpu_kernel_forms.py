@@ -1,0 +1,45 @@
+"""Kernel forms that must not change any result, forced one at a time in a
+process of their own (the switch is read once per process) and compared bit
+for bit on a set of scenes (FP32, FP32 + recheck, FP64; axis and random
+slices; bisection depths 0, 1, 4, 5, 8, 10; many hits): the bisection pass
+with one, four or eight lanes per hit (DQJ_BISECT_GROUP).  Parity with the
+oracle is covered by the other tests in the default form."""
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _render(tmp_path, **env_over):
+    tag = "_".join(f"{k}{v}" for k, v in sorted(env_over.items()))
+    out = str(tmp_path / f"forms_{tag}.npz")
+    env = dict(os.environ, **{k: str(v) for k, v in env_over.items()})
+    r = subprocess.run([sys.executable, os.path.join(HERE, "forms_worker.py"), out], env=env,
+                       cwd=os.path.dirname(HERE), capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-3000:]
+    return np.load(out)
+
+
+def _same(a, b, what):
+    assert sorted(a.files) == sorted(b.files)
+    hits = rechecks = 0
+    for k in a.files:
+        assert np.array_equal(a[k], b[k], equal_nan=True), (what, k)
+        if k.endswith("_stats"):
+            hits += int(a[k][3])
+            rechecks += int(a[k][4])
+    return hits, rechecks
+
+
+def test_bisection_forms_agree(tmp_path):
+    one = _render(tmp_path, DQJ_BISECT_GROUP=1)
+    hits, rechecks = _same(one, _render(tmp_path, DQJ_BISECT_GROUP=4), "4 lanes per hit")
+    _same(one, _render(tmp_path, DQJ_BISECT_GROUP=8), "8 lanes per hit")
+    assert hits > 100000 and rechecks > 100000  # the scenes exercise the bisection and the recheck
+
