@@ -234,8 +234,9 @@ __global__ void __launch_bounds__(kBlock) de_recheck_kernel(const __grid_constan
 }
 
 // FP64 re-trace of the pixels queued by the recheck, 32 per warp (one per
-// lane, in lockstep like de_kernel), shaded in place.
-template <int SQ, int MOD>
+// lane, in lockstep like de_kernel), shaded in place.  AXIS: an axis-aligned
+// slice, whose samples take the axis form of the first step (same results).
+template <int SQ, int MOD, bool AXIS>
 __global__ void __launch_bounds__(kBlock) de_fixup_kernel(const __grid_constant__ FrameDesc fd, const Scratch sc)
 {
     const FrameT<double> &F = fd.d;
@@ -250,7 +251,7 @@ __global__ void __launch_bounds__(kBlock) de_fixup_kernel(const __grid_constant_
         double d[3], D[8], depth;
         int n_star, esc_max;
         const bool hit =
-            de_trace_lane<double, SQ, MOD, false, false>(fd, sc, x, y, valid, st_fix, d, D, depth, n_star, esc_max);
+            de_trace_lane<double, SQ, MOD, AXIS, false>(fd, sc, x, y, valid, st_fix, d, D, depth, n_star, esc_max);
         if (valid && !hit) write_miss<double>(fd, x, y, esc_max);
         normal_shade<double, SQ, MOD>(fd, F, x, y, d, D, depth, n_star, hit, st_fix);
         st.hits += valid ? 1 : 0;
@@ -311,11 +312,16 @@ cudaError_t launch_de_t(const FrameDesc &fd, const Scratch &sc, cudaStream_t st,
     de_shade_kernel<T, SQ, MOD><<<gs > 0 ? gs : 1, kBlock, 0, st>>>(fd, sc);
     if (ev) cudaEventRecord(ev[2], st);
     if constexpr (RECHECK) {
-        static std::atomic<int> g_re{0}, g_fx{0};
+        static std::atomic<int> g_re{0}, g_fx{0}, g_fxg{0};
         de_recheck_kernel<SQ, MOD><<<num_sms * resident_per_sm(g_re, de_recheck_kernel<SQ, MOD>), kBlock, 0, st>>>(
             fd, sc);
         if (ev) cudaEventRecord(ev[3], st);
-        de_fixup_kernel<SQ, MOD><<<num_sms * resident_per_sm(g_fx, de_fixup_kernel<SQ, MOD>), kBlock, 0, st>>>(fd, sc);
+        if (fd.axis_slice)
+            de_fixup_kernel<SQ, MOD, true>
+                <<<num_sms * resident_per_sm(g_fx, de_fixup_kernel<SQ, MOD, true>), kBlock, 0, st>>>(fd, sc);
+        else
+            de_fixup_kernel<SQ, MOD, false>
+                <<<num_sms * resident_per_sm(g_fxg, de_fixup_kernel<SQ, MOD, false>), kBlock, 0, st>>>(fd, sc);
         if (ev) cudaEventRecord(ev[4], st);
     } else if (ev) {
         cudaEventRecord(ev[3], st);

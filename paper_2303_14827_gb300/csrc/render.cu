@@ -187,15 +187,18 @@ __global__ void __launch_bounds__(kBlock) march_merge_kernel(const __grid_consta
         const bool part = pixel < npx && tile % (unsigned)fd.tile_parts == (unsigned)fd.tile_part;
         int kf = -1, m = 0;
         unsigned iters = 0, samples = 0;
-        for (int r = 0; part && r < fd.k_split; ++r) {
-            const int4 e = sc.part[(int64_t)r * npx + pixel];
+        // the first range with an inside sample is part_hit (the smallest range
+        // that recorded one), so the ranges to read are known up front and
+        // their loads need not wait on one another
+        const unsigned rh = part ? __ldcg(sc.part_hit + pixel) : 0u;
+        const int nr = part ? (rh < (unsigned)fd.k_split ? (int)rh + 1 : fd.k_split) : 0;
+#pragma unroll 4
+        for (int r = 0; r < nr; ++r) {
+            const int4 e = __ldcg(sc.part + (int64_t)r * npx + pixel);
             iters += (unsigned)e.y;
             samples += (unsigned)e.w;
-            if (e.x >= 0) {
-                kf = e.x;
-                break;
-            }
-            m = max(m, e.z);
+            if (r == (int)rh) kf = e.x;
+            else m = max(m, e.z);
         }
         const bool hit = kf >= 0;
         st.iters += iters;
