@@ -581,7 +581,19 @@ class OutputPool:
 
 def served_run(ctx, reqs, arrivals, pool):
     """Submit reqs[i] at time arrivals[i] (seconds from start, sorted), poll until
-    all are done.  Returns (latencies in s, makespan s)."""
+    all are done.  Returns (latencies in s, makespan s).  Python's cyclic garbage
+    collector is paused meanwhile, so that none of its pauses lands inside a
+    measured latency."""
+    import gc
+    gc.collect()
+    gc.disable()
+    try:
+        return _served_run(ctx, reqs, arrivals, pool)
+    finally:
+        gc.enable()
+
+
+def _served_run(ctx, reqs, arrivals, pool):
     from paper_2303_14827_gb300 import binding
     n = len(reqs)
     lat = [None] * n

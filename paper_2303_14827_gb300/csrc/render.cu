@@ -213,10 +213,10 @@ __global__ void __launch_bounds__(kBlock) march_merge_kernel(const __grid_consta
 // ---------------------------------------------------------------------------
 // bisect + normal + shade over the hit list
 // ---------------------------------------------------------------------------
-// Hit lists shorter than group_below take group_lanes (4 or 8) lanes per hit
+// Hit lists shorter than group_below take group_lanes (4) lanes per hit
 // (bisect_group): one lane per hit would give the launch's warps too few hits
 // to hide the bisection's dependent chain.  Longer lists take one lane per hit
-// (the least work per hit).  All forms give the same results.
+// (the least work per hit).  Both forms give the same results.
 template <typename T, int SQ, int MOD, bool RECHECK>
 __global__ void __launch_bounds__(kBlock) bisect_kernel(const __grid_constant__ FrameDesc fd, const Scratch sc,
                                                         unsigned group_below, int group_lanes)
@@ -231,9 +231,7 @@ __global__ void __launch_bounds__(kBlock) bisect_kernel(const __grid_constant__ 
         if (lane == 0) base = atomicAdd(&sc.ctr->hit_next, per);
         base = __shfl_sync(kFull, base, 0);
         if (base >= nhits) break;
-        if (lanes == 8)
-            bisect_group<T, SQ, MOD, RECHECK, 8>(fd, sc, base, nhits, st);
-        else if (lanes == 4)
+        if (lanes == 4)
             bisect_group<T, SQ, MOD, RECHECK, 4>(fd, sc, base, nhits, st);
         else
             bisect_chunk<T, SQ, MOD, RECHECK>(fd, sc, base, nhits, st);
@@ -274,18 +272,19 @@ __global__ void __launch_bounds__(kBlock) fixup_kernel(const __grid_constant__ F
 
 // Lanes per hit of a short hit list, and the hit-list length below which a
 // list counts as short: fewer hits than 32 per resident warp of the bisection
-// launch (capb CTAs of four warps).  DQJ_BISECT_GROUP = 1, 4 or 8 forces that
-// many lanes per hit for every list.
+// launch (capb CTAs of four warps).  DQJ_BISECT_GROUP = 1 or 4 forces that
+// many lanes per hit for every list.  (Eight lanes per hit, three tree levels
+// per round, measured slower than four at every list length.)
 int bisect_forced_lanes()
 {
     static const int forced = [] {
         const char *e = std::getenv("DQJ_BISECT_GROUP");
         const long v = e ? std::strtol(e, nullptr, 10) : 0L;
-        return v == 1 || v == 4 || v == 8 ? (int)v : 0;
+        return v == 1 || v == 4 ? (int)v : 0;
     }();
     return forced;
 }
-int bisect_group_lanes() { return bisect_forced_lanes() > 1 ? bisect_forced_lanes() : 4; }
+int bisect_group_lanes() { return 4; }
 unsigned bisect_group_below(int capb)
 {
     if (bisect_forced_lanes() == 1) return 0u;
