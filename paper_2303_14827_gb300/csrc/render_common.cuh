@@ -330,9 +330,9 @@ __device__ __forceinline__ void recheck_entry(const FrameDesc &fd, const Scratch
 
 // Re-render of one pixel by one warp (all 32 lanes call), with the oracle's
 // formulas for the sample positions (the reference sequence of steps) in FP64;
-// a march sample is classified in FP32 and again in FP64 only when it is
-// marginal; bisection (five levels per round across the lanes) and normals are
-// FP64.  The lanes classify 32 consecutive march samples at a time; a ballot
+// a march or bisection sample is classified in FP32 and again in FP64 only
+// when it is marginal (the premise of the recheck mode); the bisection runs
+// five levels per round across the lanes; the normal is FP64.  The lanes classify 32 consecutive march samples at a time; a ballot
 // finds the first inside one and warp reductions give the largest escape count
 // before it, so the result and the iteration count are those of the
 // sample-by-sample loop.  Bisection runs on every lane alike; the six normal
@@ -364,11 +364,6 @@ __device__ __forceinline__ void fixup_pixel(const FrameDesc &fd, int pixel, unsi
         auto cls64 = [&](double (&z)[8]) {
             return fd.axis_slice ? classify_scalar_axis<double, SQ, MOD>(z, F, fd.max_iter)
                                  : classify_scalar<double, SQ, MOD>(z, F, fd.max_iter);
-        };
-        auto cls = [&](double t) {
-            double z[8];
-            slice(t, z);
-            return cls64(z);
         };
         // a march sample: FP32 first, FP64 only when some FP32 modulus came within
         // the recheck margin of R^2 (the premise of the recheck mode: outside the
@@ -414,8 +409,9 @@ __device__ __forceinline__ void fixup_pixel(const FrameDesc &fd, int pixel, unsi
             // Bisection, up to five levels per round: lane j - 1 holds node j of the
             // level tree (node 1 the next midpoint, children 2j: inside -> [lo, mid],
             // 2j + 1: outside -> [mid, hi]), derives its interval with the same
-            // operations as the sequential halvings and classifies its midpoint;
-            // the path is then replayed, so the bracket is the sequential one.
+            // operations as the sequential halvings and classifies its midpoint
+            // (FP32 first, FP64 when marginal, as the march samples); the path is
+            // then replayed, so the bracket is the sequential one.
             for (int b0 = 0; b0 < fd.B; b0 += 5) {
                 const int levels = min(5, fd.B - b0);
                 const int node = lane + 1;
@@ -430,7 +426,7 @@ __device__ __forceinline__ void fixup_pixel(const FrameDesc &fd, int pixel, unsi
                         else
                             h = mid;
                     }
-                    n = cls(l + 0.5 * (h - l));
+                    n = cls_march(l + 0.5 * (h - l));
                 }
                 int cur = 1;
                 for (int q = 0; q < levels; ++q) {
