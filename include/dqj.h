@@ -231,13 +231,29 @@ dqj_status dqj_render(dqj_ctx *ctx, const dqj_params *p, const dqj_outputs *out,
 dqj_status dqj_render_tiles(dqj_ctx *ctx, const dqj_params *p, const dqj_outputs *out, void *cuda_stream,
                             int32_t part, int32_t parts);
 
+/* Enqueue n frames on cuda_stream, p[i] into the device outputs out[i] (the
+ * output sets must not overlap), and return without waiting.  The frames
+ * alternate between two context-owned scratch sets and two context-owned
+ * streams forked from and joined back into cuda_stream; each frame's march
+ * starts after the previous frame's march, so a frame's bisection and FP64
+ * recheck passes run beside the next frame's march.  Results and stats equal
+ * n calls of dqj_render.  Every frame is validated before any work starts
+ * (DQJ_ERR_INVALID); n = 0 does nothing, n = 1 is dqj_render.  Ordered with
+ * the context's other renders like dqj_render.  Not under stream capture
+ * (DQJ_ERR_INVALID; capture dqj_render calls instead).  Holds a second
+ * scratch set as large as the largest frame needs.  An interface of this
+ * library (throughput of a batch of frames); the paper has no counterpart. */
+dqj_status dqj_render_batch(dqj_ctx *ctx, const dqj_params *p, const dqj_outputs *out, int32_t n,
+                            void *cuda_stream);
+
 /* Render one frame into HOST buffers: the library renders into context-owned
  * device planes, copies the requested planes to the host and waits.  Blocking. */
 dqj_status dqj_render_host(dqj_ctx *ctx, const dqj_params *p, const dqj_outputs *host_out);
 
 /* Render n frames into HOST buffers, p[i] into host_out[i], and wait.  The
  * context keeps two device plane sets, so the copy back of frame i overlaps
- * the render of frame i + 1 (use page-locked host buffers for the overlap).
+ * the render of frame i + 1 (use page-locked host buffers for the overlap);
+ * the renders themselves are pipelined as in dqj_render_batch.
  * Every frame is validated before any work starts (DQJ_ERR_INVALID); results
  * equal n calls of dqj_render_host.  n = 0 does nothing.  Blocking.  An
  * interface of this library (throughput for host-resident outputs); the paper

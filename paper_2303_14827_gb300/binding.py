@@ -123,6 +123,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         L.dqj_render.argtypes = [ctypes.c_void_p, P(dqj_params), P(dqj_outputs), ctypes.c_void_p]
         L.dqj_render_tiles.argtypes = [ctypes.c_void_p, P(dqj_params), P(dqj_outputs), ctypes.c_void_p,
                                        ctypes.c_int32, ctypes.c_int32]
+        L.dqj_render_batch.argtypes = [ctypes.c_void_p, P(dqj_params), P(dqj_outputs), ctypes.c_int32,
+                                       ctypes.c_void_p]
         L.dqj_render_host.argtypes = [ctypes.c_void_p, P(dqj_params), P(dqj_outputs)]
         L.dqj_render_host_batch.argtypes = [ctypes.c_void_p, P(dqj_params), P(dqj_outputs), ctypes.c_int32]
         L.dqj_submit.argtypes = [ctypes.c_void_p, P(dqj_params), P(dqj_outputs), P(ctypes.c_uint64)]
@@ -263,6 +265,17 @@ def tile_parts_of_pixels(ctx: int, scene: dict, parts: int):
     tiles_x = (w + tw - 1) // tw
     ys, xs = np.meshgrid(np.arange(h), np.arange(w), indexing="ij")
     return ((ys // th) * tiles_x + xs // tw) % parts
+
+
+def dqj_render_batch(ctx: int, scenes: list, outputs: list, stream: int) -> None:
+    """Enqueue scenes[i] into the DEVICE outputs outputs[i] (dqj_outputs) on
+    `stream`, frames pipelined by the library."""
+    n = len(scenes)
+    if len(outputs) != n:
+        raise ValueError("scenes and outputs differ in length")
+    ps = (dqj_params * max(n, 1))(*[make_params(s) for s in scenes])
+    os_ = (dqj_outputs * max(n, 1))(*outputs)
+    check(load().dqj_render_batch(ctypes.c_void_p(ctx), ps, os_, n, ctypes.c_void_p(stream)))
 
 
 def dqj_render_host(ctx: int, scene: dict, outputs: dqj_outputs) -> None:

@@ -397,10 +397,15 @@ void pick_tile_shape(dqj_ctx *ctx, const dqj_params &p, int &variant, int &tw, i
     }
 }
 
-// Enqueue the passes of one frame (of its tiles t with t mod parts == part);
-// ctx->mu held.
-static dqj_status enqueue_frame(dqj_ctx *ctx, const dqj_params &p, const dqj_outputs &out, cudaStream_t st,
-                                int part = 0, int parts = 1)
+// Enqueue the passes of one frame (of its tiles t with t mod parts == part) on
+// stream st with scratch set sb; ctx->mu held.  Ordered after the context's
+// previous render through ctx->done_ev unless `lane` is given: then the caller
+// (a batch) orders the frame, lane holds five events for the passes (used
+// unless the profiling ring is on), and *march_done returns the event recorded
+// after the frame's march.
+static dqj_status enqueue_frame_on(dqj_ctx *ctx, const dqj_params &p, const dqj_outputs &out, cudaStream_t st,
+                                   int part, int parts, ScratchBuf &sb, cudaEvent_t *lane,
+                                   cudaEvent_t *march_done = nullptr)
 {
     int variant, tw, th;
     pick_tile_shape(ctx, p, variant, tw, th);
@@ -433,7 +438,6 @@ static dqj_status enqueue_frame(dqj_ctx *ctx, const dqj_params &p, const dqj_out
     fd.k_chunk = (fd.N + 1 + fd.k_split - 1) / fd.k_split;
     fd.k_split = (fd.N + 1 + fd.k_chunk - 1) / fd.k_chunk;  // every range holds a sample
     const uint64_t part_entries = fd.k_split > 1 ? (uint64_t)fd.k_split * px : 0;
-    ScratchBuf &sb = ctx->scratch;
     if (capturing &&
         !(sb.base && px <= sb.pixels && (!recheck || sb.with_queue) && part_entries <= sb.part_entries))
         return fail(DQJ_ERR_INVALID, "render: under stream capture the context's scratch must already fit the frame "
@@ -456,7 +460,7 @@ static dqj_status enqueue_frame(dqj_ctx *ctx, const dqj_params &p, const dqj_out
     }
     // the previous render's event: waited on only when it was recorded in the
     // same capture state (a record inside a graph is ordered by its replays)
-    if (ctx->done_capture == (capturing ? cap_id : 0ull)) {
+    if (!lane && ctx->done_capture == (capturing ? cap_id : 0ull)) {
         e = cudaStreamWaitEvent(st, ctx->done_ev, 0);
         if (e != cudaSuccess) return cuda_fail(e, "render: cudaStreamWaitEvent");
     }
@@ -466,19 +470,90 @@ static dqj_status enqueue_frame(dqj_ctx *ctx, const dqj_params &p, const dqj_out
         e = cudaMemsetAsync(sb.view.part_hit, 0xff, px * sizeof(uint32_t), st);
         if (e != cudaSuccess) return cuda_fail(e, "render: clear split-march hits");
     }
-    cudaEvent_t *ev = nullptr;
+    cudaEvent_t *ev = lane;
     if (ctx->ring_frames > 0) ev = &ctx->ev[5 * (ctx->ring_next++ % (uint64_t)ctx->ring_frames)];
     e = launch_frame(fd, sb.view, st, ctx->num_sms, ev);
     if (e != cudaSuccess) return cuda_fail(e, "render: kernel launch");
+    if (march_done) *march_done = ev ? ev[1] : nullptr;
     if (out.stats) {
         e = cudaMemcpyAsync(out.stats, sb.view.ctr->stats, DQJ_NSTATS * sizeof(int64_t), cudaMemcpyDeviceToDevice, st);
         if (e != cudaSuccess) return cuda_fail(e, "render: stats copy");
     }
-    e = cudaEventRecord(ctx->done_ev, st);
-    if (e != cudaSuccess) return cuda_fail(e, "render: cudaEventRecord");
-    ctx->done_capture = capturing ? cap_id : 0;
+    if (!lane) {
+        e = cudaEventRecord(ctx->done_ev, st);
+        if (e != cudaSuccess) return cuda_fail(e, "render: cudaEventRecord");
+        ctx->done_capture = capturing ? cap_id : 0;
+    }
     return DQJ_OK;
 }
+
+static dqj_status enqueue_frame(dqj_ctx *ctx, const dqj_params &p, const dqj_outputs &out, cudaStream_t st,
+                                int part = 0, int parts = 1)
+{
+    return enqueue_frame_on(ctx, p, out, st, part, parts, ctx->scratch, nullptr);
+}
+
+// The frames of a batch alternate between the context's two scratch sets and
+// two lane streams, and each frame's march waits only for the previous frame's
+// march: a frame's bisection, recheck and re-render passes (short, and bound by
+// latency) run beside the next frame's march instead of after it, while the
+// marches themselves stay one at a time.  ctx->mu held from open to close.
+struct FramePipe {
+    dqj_ctx *ctx;
+    cudaEvent_t prev = nullptr;  // after the previous frame's march
+    int next = 0;
+    bool used[2] = {false, false};
+
+    // order the batch after the context's previous render and the caller's
+    // stream st, and fork the lanes from st
+    dqj_status open(cudaStream_t st)
+    {
+        cudaError_t e = cudaSuccess;
+        for (int l = 0; l < 2 && e == cudaSuccess; ++l) {
+            if (!ctx->lane_stream[l]) e = cudaStreamCreateWithFlags(&ctx->lane_stream[l], cudaStreamNonBlocking);
+            for (int k = 0; k < 5 && e == cudaSuccess; ++k)
+                if (!ctx->lane_ev[l][k]) e = cudaEventCreateWithFlags(&ctx->lane_ev[l][k], cudaEventDisableTiming);
+            if (e == cudaSuccess && !ctx->join_ev[l]) e = cudaEventCreateWithFlags(&ctx->join_ev[l], cudaEventDisableTiming);
+        }
+        if (e == cudaSuccess && !ctx->fork_ev) e = cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming);
+        if (e == cudaSuccess && ctx->done_capture == 0) e = cudaStreamWaitEvent(st, ctx->done_ev, 0);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->fork_ev, st);
+        for (int l = 0; l < 2 && e == cudaSuccess; ++l) e = cudaStreamWaitEvent(ctx->lane_stream[l], ctx->fork_ev, 0);
+        if (e != cudaSuccess) return cuda_fail(e, "render batch: lane streams");
+        return DQJ_OK;
+    }
+
+    // enqueue the next frame, after `after` too when given; *lane returns the
+    // stream it runs on
+    dqj_status frame(const dqj_params &p, const dqj_outputs &out, cudaStream_t *lane = nullptr,
+                     cudaEvent_t after = nullptr)
+    {
+        const int l = next++ & 1;
+        cudaStream_t ls = ctx->lane_stream[l];
+        cudaError_t e = cudaSuccess;
+        if (prev) e = cudaStreamWaitEvent(ls, prev, 0);
+        if (e == cudaSuccess && after) e = cudaStreamWaitEvent(ls, after, 0);
+        if (e != cudaSuccess) return cuda_fail(e, "render batch: cudaStreamWaitEvent");
+        used[l] = true;
+        if (lane) *lane = ls;
+        return enqueue_frame_on(ctx, p, out, ls, 0, 1, l ? ctx->scratch2 : ctx->scratch, ctx->lane_ev[l], &prev);
+    }
+
+    // join the lanes into st and make st the context's last render
+    dqj_status close(cudaStream_t st)
+    {
+        cudaError_t e = cudaSuccess;
+        for (int l = 0; l < 2 && e == cudaSuccess; ++l) {
+            if (!used[l]) continue;
+            e = cudaEventRecord(ctx->join_ev[l], ctx->lane_stream[l]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ctx->join_ev[l], 0);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->done_ev, st);
+        if (e != cudaSuccess) return cuda_fail(e, "render batch: join");
+        ctx->done_capture = 0;
+        return DQJ_OK;
+    }
+};
 
 dqj_status check_outputs(const dqj_params &p, const dqj_outputs *out)
 {
@@ -634,6 +709,37 @@ dqj_status dqj_render_tiles(dqj_ctx *ctx, const dqj_params *p, const dqj_outputs
     });
 }
 
+dqj_status dqj_render_batch(dqj_ctx *ctx, const dqj_params *p, const dqj_outputs *out, int32_t n, void *cuda_stream)
+{
+    return dqj::guarded([&]() -> dqj_status {
+        if (!ctx) return fail(DQJ_ERR_INVALID, "ctx is NULL");
+        if (ctx->device == DQJ_DEVICE_MOCK) return fail(DQJ_ERR_INVALID, "a mock context cannot render");
+        if (n < 0 || (n > 0 && (!p || !out))) return fail(DQJ_ERR_INVALID, "bad frame count or NULL arrays");
+        for (int32_t i = 0; i < n; ++i) {
+            dqj_status s = validate(&p[i]);
+            if (s != DQJ_OK) return s;
+            s = check_outputs(p[i], &out[i]);
+            if (s != DQJ_OK) return s;
+        }
+        if (n == 0) return DQJ_OK;
+        const cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        cudaError_t e = cudaSetDevice(ctx->device);
+        if (e != cudaSuccess) return cuda_fail(e, "render batch: cudaSetDevice");
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        e = cudaStreamIsCapturing(st, &cap);
+        if (e != cudaSuccess) return cuda_fail(e, "render batch: cudaStreamIsCapturing");
+        if (cap != cudaStreamCaptureStatusNone)
+            return fail(DQJ_ERR_INVALID, "render batch: not under stream capture (capture dqj_render calls instead)");
+        if (n == 1) return enqueue_frame(ctx, p[0], out[0], st);
+        FramePipe pipe{ctx};
+        dqj_status s = pipe.open(st);
+        for (int32_t i = 0; i < n && s == DQJ_OK; ++i) s = pipe.frame(p[i], out[i]);
+        const dqj_status c = pipe.close(st);  // joined even after a failed frame, so st stays ordered
+        return s != DQJ_OK ? s : c;
+    });
+}
+
 dqj_status dqj_render_host_batch(dqj_ctx *ctx, const dqj_params *p, const dqj_outputs *host_out, int32_t n)
 {
     return dqj::guarded([&]() -> dqj_status {
@@ -673,6 +779,13 @@ dqj_status dqj_render_host_batch(dqj_ctx *ctx, const dqj_params *p, const dqj_ou
             ctx->host_planes_bytes[b] = need;
         }
         cudaStream_t rs = ctx->host_stream, cs = ctx->host_copy_stream;
+        // two or more frames run through the frame pipeline (lane l = i % 2
+        // renders into plane set b = i % 2); one frame renders on host_stream
+        FramePipe pipe{ctx};
+        if (n > 1) {
+            const dqj_status s = pipe.open(rs);
+            if (s != DQJ_OK) return s;
+        }
         for (int32_t i = 0; i < n && e == cudaSuccess; ++i) {
             const int b = i % nbuf;
             const dqj_params &pi = p[i];
@@ -687,14 +800,21 @@ dqj_status dqj_render_host_batch(dqj_ctx *ctx, const dqj_params *p, const dqj_ou
             dev.rgba = ho.rgba ? reinterpret_cast<uint8_t *>(base + px * 20) : nullptr;
             dev.stats = ho.stats ? reinterpret_cast<int64_t *>(base + align_up(px * 24, 256)) : nullptr;
             // the render into plane set b waits for that set's previous copy back
-            e = cudaStreamWaitEvent(rs, ctx->host_copied[b], 0);
-            if (e != cudaSuccess) break;
-            dqj_status s = enqueue_frame(ctx, pi, dev, rs);
+            cudaStream_t ls = rs;
+            dqj_status s = DQJ_OK;
+            if (n > 1) {
+                s = pipe.frame(pi, dev, &ls, ctx->host_copied[b]);
+            } else {
+                e = cudaStreamWaitEvent(rs, ctx->host_copied[b], 0);
+                if (e != cudaSuccess) break;
+                s = enqueue_frame(ctx, pi, dev, rs);
+            }
             if (s != DQJ_OK) {
+                if (n > 1) pipe.close(rs);
                 cudaStreamSynchronize(cs);
                 return s;
             }
-            e = cudaEventRecord(ctx->host_rendered[b], rs);
+            e = cudaEventRecord(ctx->host_rendered[b], ls);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ctx->host_rendered[b], 0);
             const size_t w = (size_t)pi.width, hp = (size_t)ho.pitch_px;
             auto copy2d = [&](void *dst, const void *src, size_t elem) {
@@ -709,10 +829,11 @@ dqj_status dqj_render_host_batch(dqj_ctx *ctx, const dqj_params *p, const dqj_ou
                 e = cudaMemcpyAsync(ho.stats, dev.stats, DQJ_NSTATS * sizeof(int64_t), cudaMemcpyDeviceToHost, cs);
             if (e == cudaSuccess) e = cudaEventRecord(ctx->host_copied[b], cs);
         }
+        const dqj_status c = n > 1 ? pipe.close(rs) : DQJ_OK;
         const cudaError_t e2 = cudaStreamSynchronize(cs);
         if (e == cudaSuccess) e = e2;
         if (e != cudaSuccess) return cuda_fail(e, "render_host: copy back");
-        return DQJ_OK;
+        return c;
     });
 }
 

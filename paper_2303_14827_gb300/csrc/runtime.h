@@ -83,6 +83,13 @@ struct dqj_ctx {
     std::mutex tiles_mu;             // guards tiles (read by the serving thread too)
     dqj::ServeState *serve = nullptr;
     std::atomic<int> serve_policy{DQJ_SERVE_FIFO};  // order of packed requests in the persistent launch
+    // frame pipelines (dqj_render_batch, dqj_render_host_batch): a second
+    // scratch set and two lane streams, so that a frame's bisection and FP64
+    // passes run beside the next frame's march
+    dqj::ScratchBuf scratch2;
+    cudaStream_t lane_stream[2] = {nullptr, nullptr};
+    cudaEvent_t lane_ev[2][5] = {};
+    cudaEvent_t fork_ev = nullptr, join_ev[2] = {nullptr, nullptr};
     // dqj_voxelize scratch: counter block + FP64 recheck queue; grow-only
     void *vox_scratch = nullptr;
     size_t vox_bytes = 0;

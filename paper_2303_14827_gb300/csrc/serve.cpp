@@ -900,7 +900,17 @@ dqj_status dqj_destroy(dqj_ctx *ctx)
                 cudaEventSynchronize(ctx->done_ev);
             if (ctx->host_stream) cudaStreamSynchronize(ctx->host_stream);
             if (ctx->host_copy_stream) cudaStreamSynchronize(ctx->host_copy_stream);
+            for (int l = 0; l < 2; ++l)
+                if (ctx->lane_stream[l]) cudaStreamSynchronize(ctx->lane_stream[l]);
             scratch_free(ctx->scratch);
+            scratch_free(ctx->scratch2);
+            for (int l = 0; l < 2; ++l) {
+                if (ctx->lane_stream[l]) cudaStreamDestroy(ctx->lane_stream[l]);
+                for (cudaEvent_t &v : ctx->lane_ev[l])
+                    if (v) cudaEventDestroy(v);
+                if (ctx->join_ev[l]) cudaEventDestroy(ctx->join_ev[l]);
+            }
+            if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
             for (int b = 0; b < 2; ++b) {
                 if (ctx->host_planes[b]) cudaFree(ctx->host_planes[b]);
                 if (ctx->host_rendered[b]) cudaEventDestroy(ctx->host_rendered[b]);

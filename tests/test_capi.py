@@ -169,6 +169,24 @@ def test_render_host_batch_argument_errors():
         binding.dqj_destroy(ctx)
 
 
+def test_render_batch_argument_errors():
+    ctx = binding.dqj_create(-1)
+    try:
+        with pytest.raises(binding.DqjError):
+            binding.dqj_render_batch(ctx, [scenes.default_scene()] * 2, [binding.make_outputs(pitch_px=256)] * 2, 0)
+        assert "mock" in binding.last_error()
+        L = binding.load()
+        p = binding.make_params(scenes.default_scene())
+        o = binding.make_outputs(pitch_px=256)
+        c = binding.ctypes.c_void_p(ctx)
+        assert L.dqj_render_batch(c, binding.ctypes.byref(p), binding.ctypes.byref(o), -1, None) != binding.DQJ_OK
+        assert L.dqj_render_batch(c, None, None, 2, None) != binding.DQJ_OK
+        assert L.dqj_render_batch(None, binding.ctypes.byref(p), binding.ctypes.byref(o), 1, None) != binding.DQJ_OK
+        assert L.dqj_render_batch(c, None, None, 0, None) == binding.DQJ_ERR_INVALID  # mock: refused first
+    finally:
+        binding.dqj_destroy(ctx)
+
+
 def test_tile_cache_parsing_on_a_mock_context(tmp_path):
     # the cache loader keeps valid entries and ignores malformed or inconsistent
     # ones (a mock context has device name "unknown" and 0 SMs)
