@@ -68,6 +68,9 @@ __device__ __forceinline__ int classify_de(T (&z)[8], const FrameT<T> &F, int ma
             if (!__any_sync(kFull, alive)) break;
         }
     }
+    // a long orbit counts as marginal (see late_step): its FP32 count may move
+    // with the sample's position
+    if (part && max_iter > late_step<MOD>() && cnt >= late_step<MOD>()) dm = T(0);
     if (!part || alive) {
         dist = T(0);
         return 0;

@@ -27,6 +27,25 @@
 
 namespace dqj {
 
+// FP32 recheck mode: a sample whose orbit runs past late_step<MOD>() steps is
+// always rechecked in FP64, whatever its distance from R^2, and a hit whose
+// normal field takes more steps than that is re-rendered in FP64.  An FP32
+// sample position is rounded (about 6e-8 relative) and each step multiplies a
+// position difference by 2 |zeta_n|; on a long enough orbit the amplified
+// difference exceeds the recheck margin (1e-3 relative) and moves an escape
+// decision that no tested modulus came close to, and it moves the normal
+// field's central differences.  With the dual-number modulus, whose escape
+// test ignores the dual half, orbits near the real half's own Julia set run
+// long: decisions moved at steps 14-24 on 11 of 42 random frames with max_iter
+// 16-24, hence 12.  With the 8-component modulus the dual half grows with the
+// orbit's sensitivity and ends such orbits early: no decision moved in 180
+// random frames with max_iter 12-32, but normals drifted on one frame with
+// max_iter 32, hence 20.  The march kernels apply the rule for the
+// dual-number modulus only (no cost per round otherwise); the bisection, the
+// re-render and sphere tracing apply it for both.
+template <int MOD>
+__host__ __device__ constexpr int late_step() { return MOD == 1 ? 12 : 20; }
+
 __device__ __forceinline__ float dfma(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double dfma(double a, double b, double c) { return fma(a, b, c); }
 
@@ -125,6 +144,7 @@ __device__ __forceinline__ int classify_lockstep(T (&z)[8], const FrameT<T> &F, 
         cnt += alive ? 1 : 0;
         if (!__any_sync(0xffffffffu, alive)) break;
     }
+    if (RECHECK && part && max_iter > late_step<MOD>() && cnt >= late_step<MOD>()) mg = true;  // a long orbit
     marginal = mg;
     return cnt >= max_iter ? 0 : cnt + 1;
 }
@@ -171,6 +191,7 @@ __device__ __forceinline__ int classify_lockstep_it1(T (&z)[8], const FrameT<T> 
             if (!__any_sync(0xffffffffu, alive)) break;
         }
     }
+    if (RECHECK && part && max_iter > late_step<MOD>() && cnt >= late_step<MOD>()) mg = true;  // a long orbit
     marginal = mg;
     return cnt >= max_iter ? 0 : cnt + 1;
 }
@@ -222,9 +243,10 @@ __device__ __forceinline__ int classify_scalar_margin(T (&z)[8], const FrameT<T>
 {
     T sp = dq_sp<T>(z);
     marginal = false;
+    const bool long_orbits = max_iter > late_step<MOD>();  // steps past late_step count as marginal
     for (int n = 1; n <= max_iter; ++n) {
         const T m = dq_iter<T, SQ, MOD>(z, z, sp, F.c);
-        marginal = marginal || fabs(m - F.R2) <= F.margin;
+        marginal = marginal || fabs(m - F.R2) <= F.margin || (long_orbits && n > late_step<MOD>());
         if (m > F.R2) return n;
     }
     return 0;
@@ -494,6 +516,10 @@ __device__ __forceinline__ void classify_lockstep2(float2 (&z)[8], const PairCon
         v = __any_sync(0xffffffffu, aa || ab);
         if (!v) break;
     }
+    if (RECHECK && MOD == 1 && max_iter > late_step<MOD>()) {  // a long orbit is always rechecked
+        if (na >= late_step<MOD>()) dm.x = 0.f;
+        if (nb >= late_step<MOD>()) dm.y = 0.f;
+    }
     live = v;
     ca = na;
     cb = nb;
@@ -544,6 +570,10 @@ __device__ __forceinline__ void classify_lockstep2_it1(float2 (&z)[8], const Pai
             v = __any_sync(0xffffffffu, aa || ab);
             if (!v) break;
         }
+    }
+    if (RECHECK && MOD == 1 && max_iter > late_step<MOD>()) {  // a long orbit is always rechecked
+        if (na >= late_step<MOD>()) dm.x = 0.f;
+        if (nb >= late_step<MOD>()) dm.y = 0.f;
     }
     live = v;
     ca = na;

@@ -803,6 +803,9 @@ __device__ __forceinline__ void bisect_chunk(const FrameDesc &fd, const Scratch 
         }
     }
     const T depth = bis ? lo + T(0.5) * (hi - lo) : t_in;
+    // a normal field of more than late_step steps moves with the FP32 positions:
+    // the pixel is re-rendered in FP64
+    if (RECHECK && part && n_lo > late_step<MOD>()) mark_dirty(fd, sc, pixel);
     normal_shade<T, SQ, MOD>(fd, F, x, y, d, D, depth, n_lo, part, st);
     st.iters += iters;
     st.samples += samples;
@@ -920,6 +923,8 @@ __device__ __forceinline__ void bisect_group(const FrameDesc &fd, const Scratch 
         }
     }
     const T depth = bis ? lo + T(0.5) * (hi - lo) : t_in;
+    // a normal field of more than late_step steps: FP64 re-render (bisect_chunk)
+    if (RECHECK && part && j == 0 && n_lo > late_step<MOD>()) mark_dirty(fd, sc, pixel);
     // normal: evaluation q = 2a + s (F at depth -+ h e_a, s = 0: +h) runs on
     // lane q mod L of the group, in round q / L
     int nmax = part ? n_lo : 0;
