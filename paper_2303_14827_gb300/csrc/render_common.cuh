@@ -803,12 +803,61 @@ __device__ __forceinline__ void bisect_chunk(const FrameDesc &fd, const Scratch 
         }
     }
     const T depth = bis ? lo + T(0.5) * (hi - lo) : t_in;
-    // a normal field of more than late_step steps moves with the FP32 positions:
-    // the pixel is re-rendered in FP64
-    if (RECHECK && part && n_lo > late_step<MOD>()) mark_dirty(fd, sc, pixel);
-    normal_shade<T, SQ, MOD>(fd, F, x, y, d, D, depth, n_lo, part, st);
+    // RECHECK: the FP32 field of a normal of more than late_step steps carries
+    // its rounding amplified along the orbit, so those normals are evaluated in
+    // FP64 (on the FP64 ray, at the bisection's depth); the others in FP32
+    const bool n64 = RECHECK && sizeof(T) == 4 && part && n_lo > late_step<MOD>();
+    normal_shade<T, SQ, MOD>(fd, F, x, y, d, D, depth, n_lo, part && !n64, st);
+    if (RECHECK && sizeof(T) == 4 && __any_sync(kFull, n64)) {
+        const FrameT<double> &Fd = fd.d;
+        double dd[3] = {0.0, 0.0, 1.0}, ti = 0.0, to = 0.0, Dd[8];
+        if (n64) camera_clip<double>(Fd, fd.W, fd.H, x, y, dd, ti, to);
+        slice_dir<double>(Fd, dd, Dd);
+        normal_shade<double, SQ, MOD>(fd, Fd, x, y, dd, Dd, (double)depth, n_lo, n64, st);
+    }
     st.iters += iters;
     st.samples += samples;
+}
+
+// Normal and shading of the hits of an L-lane group (see bisect_group):
+// evaluation q = 2a + s (F at depth -+ h e_a, s = 0: +h) runs on lane q mod L of
+// the group, in round q / L; `part` is uniform within a group.  All 32 lanes
+// call.  Same values as normal_shade<U>.
+template <typename U, int SQ, int MOD, int L>
+__device__ __forceinline__ void group_normal(const FrameDesc &fd, const FrameT<U> &F, int x, int y, const U (&d)[3],
+                                             const U (&D)[8], U depth, int n_lo, bool part, LaneStats &st)
+{
+    const int lane = threadIdx.x & 31;
+    const int j = lane & (L - 1), gb = lane & ~(L - 1);
+    int nmax = part ? n_lo : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nmax = max(nmax, __shfl_xor_sync(kFull, nmax, o));
+    U fvq[6];
+    bool guard = false;
+#pragma unroll
+    for (int q0 = 0; q0 < 6; q0 += L) {
+        const int q = q0 + j;
+        const int a = q < 6 ? q >> 1 : 0;
+        const U hs = (q & 1) == 0 ? F.h : -F.h;
+        U z[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) z[i] = dfma(hs, F.E[a][i], dfma(depth, D[i], F.A[i]));
+        U sp = dq_sp<U>(z);
+        const int ns = part && q < 6 ? n_lo : 0;
+        for (int n = 0; n < nmax; ++n)
+            if (n < ns) dq_iter<U, SQ, MOD>(z, z, sp, F.c);
+        const U fv = modulus<U, MOD>(z);
+        const unsigned bad = __ballot_sync(kFull, q < 6 && !(fv <= normal_fmax(U(0))));
+        guard = guard || ((bad >> gb) & ((1u << L) - 1u)) != 0;
+#pragma unroll
+        for (int i = 0; i < L; ++i)
+            if (q0 + i < 6) fvq[q0 + i] = __shfl_sync(kFull, fv, gb + i);
+    }
+    if (part && j == 0) {
+        U g[3] = {fvq[0] - fvq[1], fvq[2] - fvq[3], fvq[4] - fvq[5]};
+        st.niters += 6ull * (unsigned)n_lo;
+        shade_write<U>(fd, F, x, y, n_lo, depth, g, guard, d);
+    }
 }
 
 // The same bisection, normal and shading for hit-list entries [base, base +
@@ -923,38 +972,18 @@ __device__ __forceinline__ void bisect_group(const FrameDesc &fd, const Scratch 
         }
     }
     const T depth = bis ? lo + T(0.5) * (hi - lo) : t_in;
-    // a normal field of more than late_step steps: FP64 re-render (bisect_chunk)
-    if (RECHECK && part && j == 0 && n_lo > late_step<MOD>()) mark_dirty(fd, sc, pixel);
-    // normal: evaluation q = 2a + s (F at depth -+ h e_a, s = 0: +h) runs on
-    // lane q mod L of the group, in round q / L
-    int nmax = part ? n_lo : 0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) nmax = max(nmax, __shfl_xor_sync(kFull, nmax, o));
-    T fvq[6];
-    bool guard = false;
-#pragma unroll
-    for (int q0 = 0; q0 < 6; q0 += L) {
-        const int q = q0 + j;
-        const int a = q < 6 ? q >> 1 : 0;
-        const T hs = (q & 1) == 0 ? F.h : -F.h;
-        T z[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) z[i] = dfma(hs, F.E[a][i], dfma(depth, D[i], F.A[i]));
-        T sp = dq_sp<T>(z);
-        const int ns = part && q < 6 ? n_lo : 0;
-        for (int n = 0; n < nmax; ++n)
-            if (n < ns) dq_iter<T, SQ, MOD>(z, z, sp, F.c);
-        const T fv = modulus<T, MOD>(z);
-        const unsigned bad = __ballot_sync(kFull, q < 6 && !(fv <= normal_fmax(T(0))));
-        guard = guard || ((bad >> gb) & ((1u << L) - 1u)) != 0;
-#pragma unroll
-        for (int i = 0; i < L; ++i)
-            if (q0 + i < 6) fvq[q0 + i] = __shfl_sync(kFull, fv, gb + i);
+    // RECHECK: a normal of more than late_step steps is evaluated in FP64 (see
+    // bisect_chunk), the others in T
+    const bool n64 = RECHECK && sizeof(T) == 4 && part && n_lo > late_step<MOD>();
+    group_normal<T, SQ, MOD, L>(fd, F, x, y, d, D, depth, n_lo, part && !n64, st);
+    if (RECHECK && sizeof(T) == 4 && __any_sync(kFull, n64)) {
+        const FrameT<double> &Fd = fd.d;
+        double dd[3] = {0.0, 0.0, 1.0}, ti = 0.0, to = 0.0, Dd[8];
+        if (n64) camera_clip<double>(Fd, fd.W, fd.H, x, y, dd, ti, to);
+        slice_dir<double>(Fd, dd, Dd);
+        group_normal<double, SQ, MOD, L>(fd, Fd, x, y, dd, Dd, (double)depth, n_lo, n64, st);
     }
     if (part && j == 0) {
-        T g[3] = {fvq[0] - fvq[1], fvq[2] - fvq[3], fvq[4] - fvq[5]};
-        st.niters += 6ull * (unsigned)n_lo;
-        shade_write<T>(fd, F, x, y, n_lo, depth, g, guard, d);
         st.iters += iters;
         st.samples += samples;
         if (RECHECK) st.rechecks += rechecks;

@@ -23,6 +23,10 @@ def scenes_list():
                                     precision=scenes.PRECISION_FP32_RECHECK))
     out.append(scenes.default_scene(width=1920, height=1080, max_iter=16, march_steps=512, bisect_steps=10,
                                     precision=scenes.PRECISION_FP32_RECHECK))
+    # long orbits: normals of more than the late step evaluated in FP64
+    out.append(scenes.default_scene(width=320, height=240, max_iter=32, precision=scenes.PRECISION_FP32_RECHECK))
+    out.append(scenes.default_scene(width=320, height=240, max_iter=20, modulus_mode=scenes.MODULUS_DUALNUM,
+                                    precision=scenes.PRECISION_FP32_RECHECK))
     return out
 
 
