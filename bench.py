@@ -352,8 +352,12 @@ def run_gpu(args, world, rank, local):
     outs = [binding.alloc_outputs(W, H, device=f"cuda:{local}") for _ in frames]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{local}")
     peak, basis = fp32_peak_tflops(local)
-    kname = {0: "march2_kernel<ALGEBRAIC,EUCLID8,plain,axis>", 1: "march2_kernel<ALGEBRAIC,EUCLID8,recheck,axis>",
-             2: "march_kernel<double,ALGEBRAIC,EUCLID8>"}
+    # the axis-slice march: two samples of each ray per round unless DQJ_MARCH_SAMPLES=1
+    if os.environ.get("DQJ_MARCH_SAMPLES", "").strip() == "1":
+        kname = {0: "march2_kernel<ALGEBRAIC,EUCLID8,plain,axis>", 1: "march2_kernel<ALGEBRAIC,EUCLID8,recheck,axis>"}
+    else:
+        kname = {0: "march4_kernel<ALGEBRAIC,EUCLID8,plain>", 1: "march4_kernel<ALGEBRAIC,EUCLID8,recheck>"}
+    kname[2] = "march_kernel<double,ALGEBRAIC,EUCLID8>"
 
     # the headline: the workload frames in the requested mode (default: FP32 + FP64 recheck)
     ms, st, pass_ms, clocks = timed_frames(ctx, frames, outs, args.steps, args.warmup, local, world, flush)

@@ -457,10 +457,16 @@ __device__ __forceinline__ float2 dq_iter2_axis_first(const float2 (&zi)[8], flo
 // (components 3..7 are zero) and the first step takes dq_iter2_axis_first.
 // `live` (warp-uniform) is false when the warp's last vote saw no bounded half:
 // then no half is inside.
-// RECHECK: dm returns, per half with a sample, the smallest distance of a
-// tested modulus from R^2, up to and including the escaping one: the sample is
-// marginal when dm <= P.margin_t.  Each later step costs one paired
-// subtraction and a predicated minimum per half; the axis-form first step
+// RECHECK: dm returns, per half with a sample, the smallest distance from R^2
+// of its tested moduli, up to and including the escaping one, and of the
+// moduli of the steps the half takes after escaping while other halves of the
+// warp are still bounded: the sample is marginal when dm <= P.margin_t.  Each
+// later step costs one paired subtraction and a minimum per half; taking the
+// minimum only while the half is bounded cost 4 % of the march.  A modulus
+// after the escape that comes within the band (about 2e-4 of the flagged
+// samples) only adds a recheck, which confirms the FP32 count, so the flagged
+// set, but not the result, depends on how many samples share the warp's
+// steps.  The axis-form first step
 // measures |a - a_c| instead (see PairConsts), for every half alike, so a half
 // without a sample must carry a z whose first step is far outside the band
 // (march2_tile gives it a ray parameter of 1e18: a = +inf).  Without AXIS such
@@ -578,6 +584,86 @@ __device__ __forceinline__ void classify_lockstep2_it1(float2 (&z)[8], const Pai
     live = v;
     ca = na;
     cb = nb;
+}
+
+// classify_lockstep2 (AXIS form) for two samples of each of a lane's two rays
+// at once: set 0 (z; halves a, b) and set 1 (y; halves a2, b2).  The sets
+// advance in the same steps with one vote per step over all four halves, so
+// per sample the vote, the loop and the round's bookkeeping cost half as
+// much, and the two sets' independent chains hide each other's latency.  Each
+// half's outputs are those classify_lockstep2 gives it alone (the same
+// operations on its own values; a half only stops counting earlier or later).
+template <int SQ, int MOD, bool RECHECK>
+__device__ __forceinline__ void classify_lockstep4_axis(float2 (&z)[8], float2 (&y)[8], const PairConsts &P, float R2,
+                                                        int max_iter, bool &aa, bool &ab, bool &aa2, bool &ab2,
+                                                        int &ca, int &cb, int &ca2, int &cb2, float2 &dm,
+                                                        float2 &dm2, bool &live)
+{
+    bool v = true;
+    int na = 0, nb = 0, na2 = 0, nb2 = 0;
+    float2 sp = f2fma(z[2], z[2], f2mul(z[1], z[1]));
+    float2 sq = f2fma(y[2], y[2], f2mul(y[1], y[1]));
+    float2 w[8], u[8];
+    auto test = [&](float2 x, float2 x2) {
+        if (RECHECK) {  // as in classify_lockstep2: every step, no predicate
+            const float2 e = f2add(x, P.negR2), e2 = f2add(x2, P.negR2);
+            dm.x = fminf(dm.x, fabsf(e.x));
+            dm.y = fminf(dm.y, fabsf(e.y));
+            dm2.x = fminf(dm2.x, fabsf(e2.x));
+            dm2.y = fminf(dm2.y, fabsf(e2.y));
+        }
+        aa = aa && (x.x <= R2);
+        ab = ab && (x.y <= R2);
+        aa2 = aa2 && (x2.x <= R2);
+        ab2 = ab2 && (x2.y <= R2);
+        na += aa ? 1 : 0;
+        nb += ab ? 1 : 0;
+        na2 += aa2 ? 1 : 0;
+        nb2 += ab2 ? 1 : 0;
+    };
+    int n0 = max_iter;
+    {
+        const float2 a = dq_iter2_axis_first(z, w, sp, P);
+        const float2 a2 = dq_iter2_axis_first(y, u, sq, P);
+        if (RECHECK) {  // halves without a sample come with a far-away z (see march2_tile)
+            const float2 e = f2add(a, P.neg_ac), e2 = f2add(a2, P.neg_ac);
+            dm = make_float2(fabsf(e.x), fabsf(e.y));
+            dm2 = make_float2(fabsf(e2.x), fabsf(e2.y));
+        }
+        aa = aa && (a.x < P.t_esc);
+        ab = ab && (a.y < P.t_esc);
+        aa2 = aa2 && (a2.x < P.t_esc);
+        ab2 = ab2 && (a2.y < P.t_esc);
+        na += aa ? 1 : 0;
+        nb += ab ? 1 : 0;
+        na2 += aa2 ? 1 : 0;
+        nb2 += ab2 ? 1 : 0;
+        v = __any_sync(0xffffffffu, aa || ab || aa2 || ab2);
+        if (v && max_iter > 1) {
+            test(dq_iter2<SQ, MOD>(w, z, sp, P), dq_iter2<SQ, MOD>(u, y, sq, P));
+            v = __any_sync(0xffffffffu, aa || ab || aa2 || ab2);
+            if (v) n0 = 2;
+        }
+    }
+    for (int n = n0; n < max_iter; n += 2) {
+        test(dq_iter2<SQ, MOD>(z, w, sp, P), dq_iter2<SQ, MOD>(y, u, sq, P));
+        v = __any_sync(0xffffffffu, aa || ab || aa2 || ab2);
+        if (!v || n + 1 >= max_iter) break;
+        test(dq_iter2<SQ, MOD>(w, z, sp, P), dq_iter2<SQ, MOD>(u, y, sq, P));
+        v = __any_sync(0xffffffffu, aa || ab || aa2 || ab2);
+        if (!v) break;
+    }
+    if (RECHECK && MOD == 1 && max_iter > late_step<MOD>()) {  // a long orbit is always rechecked
+        if (na >= late_step<MOD>()) dm.x = 0.f;
+        if (nb >= late_step<MOD>()) dm.y = 0.f;
+        if (na2 >= late_step<MOD>()) dm2.x = 0.f;
+        if (nb2 >= late_step<MOD>()) dm2.y = 0.f;
+    }
+    live = v;
+    ca = na;
+    cb = nb;
+    ca2 = na2;
+    cb2 = nb2;
 }
 
 }  // namespace dqj

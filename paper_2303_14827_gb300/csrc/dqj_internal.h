@@ -79,6 +79,7 @@ struct alignas(16) FrameDesc {
     int32_t k_chunk;      // samples per range
     int32_t tile_part;    // the frame's tiles t with t mod tile_parts == tile_part are rendered
     int32_t tile_parts;   // (1: every tile)
+    int32_t march_samples;  // paired FP32 march on an axis-aligned slice: samples of each ray per round (1, 2)
 };
 
 // Counters at the head of the scratch block; zeroed before every frame.
@@ -123,5 +124,9 @@ cudaError_t fma_peak_launch(int variant, int num_sms, float *sink, cudaStream_t 
 // Ranges the paired FP32 march of a frame splits its samples into (1: none):
 // enough for the frame's tiles to fill the resident warps of num_sms SMs.
 int march_split(const FrameDesc &fd, int num_sms);
+// Samples of each ray per round of the paired FP32 march on an axis-aligned
+// slice: 2 unless DQJ_MARCH_SAMPLES = 1 (read once per process).  Both give
+// the same results.
+int march_samples_per_round();
 
 }  // namespace dqj

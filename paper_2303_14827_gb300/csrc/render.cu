@@ -143,6 +143,27 @@ __global__ void __launch_bounds__(kBlock, AXIS ? 5 : 4)  // the general form kee
     }
 }
 
+// march2_kernel on an axis-aligned slice, two samples of each ray per round
+// (march4_tile).  Its four sets of iterates take more registers: four CTAs
+// per SM.
+template <int SQ, int MOD, bool RECHECK>
+__global__ void __launch_bounds__(kBlock, 4) march4_kernel(const __grid_constant__ FrameDesc fd, const Scratch sc)
+{
+    __shared__ int4 stage[RECHECK ? kBlock / 32 : 1][RECHECK ? kQStage : 1];  // recheck entries, per warp
+    const int lane = threadIdx.x & 31;
+    const unsigned ntiles = subset_tiles(fd, (unsigned)fd.tiles_x * (unsigned)fd.tiles_y);
+    for (;;) {
+        unsigned tile = 0;
+        if (lane == 0) tile = atomicAdd(&sc.ctr->tile_next, 1u);
+        tile = __shfl_sync(kFull, tile, 0);
+        if (tile >= ntiles) break;
+        tile = subset_tile(fd, tile);
+        LaneStats st;
+        march4_tile<SQ, MOD, RECHECK>(fd, fd.p2, sc, tile, st, stage[RECHECK ? threadIdx.x >> 5 : 0]);
+        flush_lane_stats<false>(sc, st, true);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // split march, for frames with fewer tiles than the GPU has resident warps: a
 // work item is one 64-ray tile and one of fd.k_split contiguous ranges of the
@@ -318,7 +339,12 @@ cudaError_t launch_passes(const FrameDesc &fd, const Scratch &sc, cudaStream_t s
         if (fd.march_variant == 1 && !(fd.k_split > 1 && !RECHECK)) {
             // a persistent grid per instantiation: the axis and general forms
             // have different register counts and resident CTAs per SM
-            if (fd.axis_slice) {
+            if (fd.axis_slice && fd.march_samples == 2) {
+                static std::atomic<int> g_march4{0};
+                const int cap = num_sms * resident_per_sm(g_march4, march4_kernel<SQ, MOD, RECHECK>);
+                const int gm = (int)min((unsigned)cap, (ntiles + 3u) / 4u);
+                march4_kernel<SQ, MOD, RECHECK><<<gm > 0 ? gm : 1, kBlock, 0, st>>>(fd, sc);
+            } else if (fd.axis_slice) {
                 const int cap = num_sms * resident_per_sm(g_march2a, march2_kernel<SQ, MOD, RECHECK, true>);
                 const int gm = (int)min((unsigned)cap, (ntiles + 3u) / 4u);
                 march2_kernel<SQ, MOD, RECHECK, true><<<gm > 0 ? gm : 1, kBlock, 0, st>>>(fd, sc);
@@ -365,6 +391,15 @@ cudaError_t launch_mode(const FrameDesc &fd, const Scratch &sc, cudaStream_t st,
 }
 
 }  // namespace
+
+int march_samples_per_round()
+{
+    static const int n = [] {
+        const char *e = std::getenv("DQJ_MARCH_SAMPLES");
+        return e && std::strtol(e, nullptr, 10) == 1 ? 1 : 2;
+    }();
+    return n;
+}
 
 int march_split(const FrameDesc &fd, int num_sms)
 {

@@ -687,6 +687,135 @@ __device__ __forceinline__ void march2_tile(const FrameDesc &fd, const PairConst
     warp_push(hitb, make_int4(yb * fd.W + xb, kfb, 0, 0), sc.hits, sc.hit_cap, &sc.ctr->hit_count);
 }
 
+// march2_tile on an axis-aligned slice with two samples of each ray per round
+// (samples k and k + 1, classify_lockstep4_axis): the same per-sample
+// arithmetic, so the same results, iteration counts and recheck entries.  A
+// sample k + 1 after an inside sample k is classified but not counted or
+// staged, as the one-sample march never reaches it.  Not used for the split
+// march.
+template <int SQ, int MOD, bool RECHECK>
+__device__ __forceinline__ void march4_tile(const FrameDesc &fd, const PairConsts &P, const Scratch &sc, unsigned tile,
+                                            LaneStats &st, int4 *qs = nullptr)
+{
+    const FrameT<float> &F = fd.f;
+    const int lane = threadIdx.x & 31;
+    const int N = fd.N, max_iter = fd.max_iter;
+    const int tx = (int)(tile % (unsigned)fd.tiles_x), ty = (int)(tile / (unsigned)fd.tiles_x);
+    auto px = [&](int slot) { return tx * fd.tile_w + slot % fd.tile_w; };
+    auto py = [&](int slot) { return ty * fd.tile_h + slot / fd.tile_w; };
+    int pixa = 0, pixb = 0;
+    bool acta, actb;
+    float2 D[3], tin, dl;
+    {
+        const int xa = px(lane), ya = py(lane), xb = px(lane + 32), yb = py(lane + 32);
+        if (RECHECK) {
+            pixa = ya * fd.W + xa;
+            pixb = yb * fd.W + xb;
+        }
+        const bool va = xa < fd.W && ya < fd.H, vb = xb < fd.W && yb < fd.H;
+        float da[3] = {0.f, 0.f, 1.f}, db[3] = {0.f, 0.f, 1.f};
+        float tia = 0.f, toa = 0.f, tib = 0.f, tob = 0.f;
+        acta = va && camera_clip<float>(F, fd.W, fd.H, xa, ya, da, tia, toa);
+        actb = vb && camera_clip<float>(F, fd.W, fd.H, xb, yb, db, tib, tob);
+        if (!acta) tia = toa = 0.f;
+        if (!actb) tib = tob = 0.f;
+        dl = make_float2((toa - tia) / (float)N, (tob - tib) / (float)N);
+        if (RECHECK) {  // a half without a ray samples far away: never within the recheck band
+            if (!acta) tia = kFarT;
+            if (!actb) tib = kFarT;
+        }
+        float Da[8], Db[8];
+        slice_dir<float>(F, da, Da);
+        slice_dir<float>(F, db, Db);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) D[i] = make_float2(Da[i], Db[i]);
+        tin = make_float2(tia, tib);
+    }
+    const bool boxa = acta, boxb = actb;
+    int suma = 0, sumb = 0, maxa = 0, maxb = 0, kfa = -1, kfb = -1;
+    int qn = 0;  // staged recheck entries (warp-uniform)
+    const int k1 = N + 1;
+    float2 kf = make_float2(0.f, 0.f);
+    const float2 one = make_float2(1.f, 1.f), two = make_float2(2.f, 2.f), far = make_float2(kFarT, kFarT);
+    bool more = __any_sync(kFull, acta || actb);
+    for (int k = 0; k < k1 && more; k += 2) {
+        const bool has2 = k + 1 < k1;  // warp-uniform: the last round of an even count has one sample
+        const float2 t = f2fma(kf, dl, tin);
+        const float2 t2 = has2 ? f2fma(f2add(kf, one), dl, tin) : far;
+        kf = f2add(kf, two);
+        float2 z[8], y[8];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            z[i] = f2fma(t, D[i], P.A[i]);
+            y[i] = f2fma(t2, D[i], P.A[i]);
+        }
+        bool ina = acta, inb = actb, ina2 = acta && has2, inb2 = actb && has2, live;
+        int ca, cb, ca2, cb2;
+        float2 dm, dm2;
+        classify_lockstep4_axis<SQ, MOD, RECHECK>(z, y, P, F.R2, max_iter, ina, inb, ina2, inb2, ca, cb, ca2, cb2,
+                                                  dm, dm2, live);
+        if (RECHECK && __any_sync(kFull, fminf(fminf(dm.x, dm.y), fminf(dm2.x, dm2.y)) <= P.margin_t)) {
+            // marginal samples in this round (rare): stage sample k's, then sample k + 1's
+            const unsigned below = (1u << lane) - 1u;
+            {
+                const bool pa = acta && dm.x <= P.margin_t, pb = actb && dm.y <= P.margin_t;
+                const unsigned ba = __ballot_sync(kFull, pa), bb = __ballot_sync(kFull, pb);
+                const int nqa = __popc(ba);
+                if (pa) qs[qn + __popc(ba & below)] = make_int4(pixa, k | (kMarchSample << 16), 0, ina ? 0 : ca + 1);
+                if (pb) qs[qn + nqa + __popc(bb & below)] = make_int4(pixb, k | (kMarchSample << 16), 0, inb ? 0 : cb + 1);
+                qn += nqa + __popc(bb);
+                if (qn > kQStage - 64) {
+                    flush_staged(fd, sc, qs, qn);
+                    qn = 0;
+                }
+            }
+            {
+                const bool pa = acta && has2 && !ina && dm2.x <= P.margin_t;
+                const bool pb = actb && has2 && !inb && dm2.y <= P.margin_t;
+                const unsigned ba = __ballot_sync(kFull, pa), bb = __ballot_sync(kFull, pb);
+                const int nqa = __popc(ba);
+                const int k2 = k + 1;
+                if (pa) qs[qn + __popc(ba & below)] = make_int4(pixa, k2 | (kMarchSample << 16), 0, ina2 ? 0 : ca2 + 1);
+                if (pb) qs[qn + nqa + __popc(bb & below)] = make_int4(pixb, k2 | (kMarchSample << 16), 0, inb2 ? 0 : cb2 + 1);
+                qn += nqa + __popc(bb);
+                if (qn > kQStage - 64) {
+                    flush_staged(fd, sc, qs, qn);
+                    qn = 0;
+                }
+            }
+        }
+        // sample k + 1 counts only after an outside sample k (ca2 = 0 without a sample)
+        suma += ca + (ina ? 0 : ca2);
+        sumb += cb + (inb ? 0 : cb2);
+        maxa = max(maxa, max(ca, ina ? 0 : ca2));
+        maxb = max(maxb, max(cb, inb ? 0 : cb2));
+        if (live) {  // some half stayed bounded: those rays are inside at sample k or k + 1
+            const bool da = ina || ina2, db = inb || inb2;
+            if (da) kfa = ina ? k : k + 1;
+            if (db) kfb = inb ? k : k + 1;
+            if (RECHECK) {  // a finished ray samples far away from now on (see above)
+                if (da) tin.x = kFarT;
+                if (db) tin.y = kFarT;
+            }
+            acta = acta && !da;
+            actb = actb && !db;
+            more = __any_sync(kFull, acta || actb);
+        }
+    }
+    if (RECHECK && qn > 0) recheck_staged<SQ, MOD>(fd, sc, qs, qn);
+    const bool hita = kfa >= 0, hitb = kfb >= 0;
+    const int nesca = hita ? kfa : k1, nescb = hitb ? kfb : k1;
+    st.iters += (boxa ? suma + nesca : 0) + (boxb ? sumb + nescb : 0);
+    st.samples += (boxa ? nesca + (hita ? 1 : 0) : 0) + (boxb ? nescb + (hitb ? 1 : 0) : 0);
+    st.hits += (hita ? 1 : 0) + (hitb ? 1 : 0);
+    const int xa = px(lane), ya = py(lane), xb = px(lane + 32), yb = py(lane + 32);
+    const bool va = xa < fd.W && ya < fd.H, vb = xb < fd.W && yb < fd.H;
+    if (va && !hita) write_miss<float>(fd, xa, ya, boxa ? maxa + 1 : 0);
+    if (vb && !hitb) write_miss<float>(fd, xb, yb, boxb ? maxb + 1 : 0);
+    warp_push(hita, make_int4(ya * fd.W + xa, kfa, 0, 0), sc.hits, sc.hit_cap, &sc.ctr->hit_count);
+    warp_push(hitb, make_int4(yb * fd.W + xb, kfb, 0, 0), sc.hits, sc.hit_cap, &sc.ctr->hit_count);
+}
+
 // Normal (central differences of F(p) = modulus(zeta_{n*}(p)) at p +- h e_a,
 // iterated n* times from zeta0 = A + depth D +- h E_a, the slice image of
 // eye + depth d +- h e_a), shading and the pixel's outputs for a hit at depth;

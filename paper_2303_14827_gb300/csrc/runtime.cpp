@@ -297,6 +297,7 @@ void derive_frame(const dqj_params &p, FrameDesc &fd, int tile_w, int tile_h)
     fd.k_chunk = fd.N + 1;
     fd.tile_part = 0;
     fd.tile_parts = 1;
+    fd.march_samples = march_samples_per_round();
 }
 
 static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }

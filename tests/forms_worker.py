@@ -1,5 +1,6 @@
 """Renders the scenes of tests/test_gpu_kernel_forms.py in a process whose
-kernel-form switch (DQJ_BISECT_GROUP, read once per process) the test sets, and
+kernel-form switches (DQJ_BISECT_GROUP, DQJ_MARCH_SAMPLES; read once per
+process) the test sets, and
 saves the output planes and counters."""
 import os
 import sys
@@ -27,6 +28,19 @@ def scenes_list():
     out.append(scenes.default_scene(width=320, height=240, max_iter=32, precision=scenes.PRECISION_FP32_RECHECK))
     out.append(scenes.default_scene(width=320, height=240, max_iter=20, modulus_mode=scenes.MODULUS_DUALNUM,
                                     precision=scenes.PRECISION_FP32_RECHECK))
+    # march rounds of two samples per ray: even and odd sample counts, one or
+    # two or three samples in all, one or two steps, the dual-number modulus
+    for prec in (scenes.PRECISION_FP32, scenes.PRECISION_FP32_RECHECK):
+        out.append(scenes.default_scene(width=77, height=45, march_steps=255, precision=prec))
+        out.append(scenes.default_scene(width=40, height=24, march_steps=1, precision=prec))
+        out.append(scenes.default_scene(width=40, height=24, march_steps=2, precision=prec))
+        out.append(scenes.default_scene(width=64, height=40, max_iter=1, precision=prec))
+        out.append(scenes.default_scene(width=64, height=40, max_iter=2, march_steps=100, precision=prec))
+        out.append(scenes.default_scene(width=96, height=64, max_iter=8, modulus_mode=scenes.MODULUS_DUALNUM,
+                                        precision=prec))
+    # FP32 frames with more tiles than resident warps take the unsplit march
+    out.append(scenes.default_scene(width=640, height=480, precision=scenes.PRECISION_FP32))
+    out.append(scenes.default_scene(width=641, height=483, march_steps=255, precision=scenes.PRECISION_FP32))
     return out
 
 

@@ -1,8 +1,10 @@
 """Kernel forms that must not change any result, forced one at a time in a
 process of their own (the switch is read once per process) and compared bit
 for bit on a set of scenes (FP32, FP32 + recheck, FP64; axis and random
-slices; bisection depths 0, 1, 4, 5, 8, 10; many hits): the bisection pass
-with one or four lanes per hit (DQJ_BISECT_GROUP).  Parity with the
+slices; bisection depths 0, 1, 4, 5, 8, 10; many hits; odd and even sample
+counts): the bisection pass with one or four lanes per hit
+(DQJ_BISECT_GROUP), and the axis-slice march with one or two samples of each
+ray per round (DQJ_MARCH_SAMPLES).  Parity with the
 oracle is covered by the other tests in the default form."""
 import os
 import subprocess
@@ -26,11 +28,19 @@ def _render(tmp_path, **env_over):
     return np.load(out)
 
 
-def _same(a, b, what):
+def _same(a, b, what, recheck_counter=True):
+    """Every plane and counter equal; without recheck_counter the recheck
+    counter (stats[4]) may differ by 0.1 %: it also counts samples flagged by a
+    modulus taken after their escape, and how many such steps a sample takes
+    depends on how many samples share the warp's steps."""
     assert sorted(a.files) == sorted(b.files)
     hits = rechecks = 0
     for k in a.files:
-        assert np.array_equal(a[k], b[k], equal_nan=True), (what, k)
+        x, y = a[k], b[k]
+        if k.endswith("_stats") and not recheck_counter:
+            assert abs(int(x[4]) - int(y[4])) <= max(2, int(x[4]) // 1000), (what, k, x, y)
+            x, y = np.delete(x, 4), np.delete(y, 4)
+        assert np.array_equal(x, y, equal_nan=True), (what, k)
         if k.endswith("_stats"):
             hits += int(a[k][3])
             rechecks += int(a[k][4])
@@ -42,3 +52,10 @@ def test_bisection_forms_agree(tmp_path):
     hits, rechecks = _same(one, _render(tmp_path, DQJ_BISECT_GROUP=4), "4 lanes per hit")
     assert hits > 100000 and rechecks > 100000  # the scenes exercise the bisection and the recheck
 
+
+
+def test_march_forms_agree(tmp_path):
+    one = _render(tmp_path, DQJ_MARCH_SAMPLES=1)
+    hits, rechecks = _same(one, _render(tmp_path, DQJ_MARCH_SAMPLES=2), "two samples per round",
+                           recheck_counter=False)
+    assert hits > 100000 and rechecks > 100000
