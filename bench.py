@@ -51,7 +51,7 @@ MODE_NAMES = {0: "FP32", 1: "FP32 + FP64 recheck (margin 1e-3)", 2: "FP64"}
 DTYPES = {0: "f32", 1: "f32+f64-recheck", 2: "f64"}
 KERNEL_SOURCES = ("paper_2303_14827_gb300/csrc/render.cu", "paper_2303_14827_gb300/csrc/render_common.cuh",
                   "paper_2303_14827_gb300/csrc/dq_math.cuh", "paper_2303_14827_gb300/csrc/dqj_internal.h")
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "march_kernel_1080p.md")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "march4_kernel_1080p.md")
 
 
 def kernel_sha() -> str:
@@ -352,12 +352,10 @@ def run_gpu(args, world, rank, local):
     outs = [binding.alloc_outputs(W, H, device=f"cuda:{local}") for _ in frames]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{local}")
     peak, basis = fp32_peak_tflops(local)
-    # the axis-slice march: two samples of each ray per round unless DQJ_MARCH_SAMPLES=1
-    if os.environ.get("DQJ_MARCH_SAMPLES", "").strip() == "1":
-        kname = {0: "march2_kernel<ALGEBRAIC,EUCLID8,plain,axis>", 1: "march2_kernel<ALGEBRAIC,EUCLID8,recheck,axis>"}
-    else:
-        kname = {0: "march4_kernel<ALGEBRAIC,EUCLID8,plain>", 1: "march4_kernel<ALGEBRAIC,EUCLID8,recheck>"}
-    kname[2] = "march_kernel<double,ALGEBRAIC,EUCLID8>"
+    # the paired march: two samples of each ray per round unless DQJ_MARCH_SAMPLES=1
+    k2 = "march2_kernel" if os.environ.get("DQJ_MARCH_SAMPLES", "").strip() == "1" else "march4_kernel"
+    kname = {0: f"{k2}<ALGEBRAIC,EUCLID8,plain,axis>", 1: f"{k2}<ALGEBRAIC,EUCLID8,recheck,axis>",
+             2: "march_kernel<double,ALGEBRAIC,EUCLID8>"}
 
     # the headline: the workload frames in the requested mode (default: FP32 + FP64 recheck)
     ms, st, pass_ms, clocks = timed_frames(ctx, frames, outs, args.steps, args.warmup, local, world, flush)
@@ -404,7 +402,7 @@ def run_gpu(args, world, rank, local):
     for p, tag in ((1, "recheck"), (0, "plain")):
         fr = [dict(g, precision=p) for g in gen]
         sec, _, _, _, _ = mode_section(ctx, fr, outs[:3], max(3, args.steps // 3), args.warmup, local, world,
-                                       flush, peak, basis, f"march2_kernel<ALGEBRAIC,EUCLID8,{tag},general>",
+                                       flush, peak, basis, f"{k2}<ALGEBRAIC,EUCLID8,{tag},general>",
                                        "general_" + tag)
         gsec[tag] = sec
     line["general_slice"] = gsec

@@ -666,4 +666,70 @@ __device__ __forceinline__ void classify_lockstep4_axis(float2 (&z)[8], float2 (
     cb2 = nb2;
 }
 
+// classify_lockstep2_it1 for two samples of each of a lane's two rays at once
+// (see classify_lockstep4_axis): z and y hold the first iterates of samples
+// k and k + 1.  Same outputs per half as classify_lockstep2_it1.
+template <int SQ, int MOD, bool RECHECK>
+__device__ __forceinline__ void classify_lockstep4_it1(float2 (&z)[8], float2 (&y)[8], const PairConsts &P, float R2,
+                                                       int max_iter, bool &aa, bool &ab, bool &aa2, bool &ab2,
+                                                       int &ca, int &cb, int &ca2, int &cb2, float2 &dm,
+                                                       float2 &dm2, bool &live)
+{
+    const float inf = __int_as_float(0x7f800000);
+    dm = dm2 = make_float2(inf, inf);
+    int na = 0, nb = 0, na2 = 0, nb2 = 0;
+    float2 sp = dq_sp2(z), sq = dq_sp2(y);
+    float2 w[8], u[8];
+    auto test = [&](float2 x, float2 x2) {
+        if (RECHECK) {  // as in classify_lockstep2: every step, no predicate
+            const float2 e = f2add(x, P.negR2), e2 = f2add(x2, P.negR2);
+            dm.x = fminf(dm.x, fabsf(e.x));
+            dm.y = fminf(dm.y, fabsf(e.y));
+            dm2.x = fminf(dm2.x, fabsf(e2.x));
+            dm2.y = fminf(dm2.y, fabsf(e2.y));
+        }
+        aa = aa && (x.x <= R2);
+        ab = ab && (x.y <= R2);
+        aa2 = aa2 && (x2.x <= R2);
+        ab2 = ab2 && (x2.y <= R2);
+        na += aa ? 1 : 0;
+        nb += ab ? 1 : 0;
+        na2 += aa2 ? 1 : 0;
+        nb2 += ab2 ? 1 : 0;
+    };
+    {
+        float2 x = f2fma(z[0], z[0], sp), x2 = f2fma(y[0], y[0], sq);
+        if (MOD == 0) {
+#pragma unroll
+            for (int i = 4; i < 8; ++i) {
+                x = f2fma(z[i], z[i], x);
+                x2 = f2fma(y[i], y[i], x2);
+            }
+        }
+        test(x, x2);
+    }
+    bool v = __any_sync(0xffffffffu, aa || ab || aa2 || ab2);
+    if (v) {
+        for (int n = 1; n < max_iter; n += 2) {
+            test(dq_iter2<SQ, MOD>(z, w, sp, P), dq_iter2<SQ, MOD>(y, u, sq, P));
+            v = __any_sync(0xffffffffu, aa || ab || aa2 || ab2);
+            if (!v || n + 1 >= max_iter) break;
+            test(dq_iter2<SQ, MOD>(w, z, sp, P), dq_iter2<SQ, MOD>(u, y, sq, P));
+            v = __any_sync(0xffffffffu, aa || ab || aa2 || ab2);
+            if (!v) break;
+        }
+    }
+    if (RECHECK && MOD == 1 && max_iter > late_step<MOD>()) {  // a long orbit is always rechecked
+        if (na >= late_step<MOD>()) dm.x = 0.f;
+        if (nb >= late_step<MOD>()) dm.y = 0.f;
+        if (na2 >= late_step<MOD>()) dm2.x = 0.f;
+        if (nb2 >= late_step<MOD>()) dm2.y = 0.f;
+    }
+    live = v;
+    ca = na;
+    cb = nb;
+    ca2 = na2;
+    cb2 = nb2;
+}
+
 }  // namespace dqj

@@ -143,11 +143,12 @@ __global__ void __launch_bounds__(kBlock, AXIS ? 5 : 4)  // the general form kee
     }
 }
 
-// march2_kernel on an axis-aligned slice, two samples of each ray per round
-// (march4_tile).  Its four sets of iterates take more registers: four CTAs
-// per SM.
-template <int SQ, int MOD, bool RECHECK>
-__global__ void __launch_bounds__(kBlock, 4) march4_kernel(const __grid_constant__ FrameDesc fd, const Scratch sc)
+// march2_kernel with two samples of each ray per round (march4_tile).  Its
+// four sets of iterates take more registers: four CTAs per SM on an axis
+// slice, three with the general form's first-iterate coefficients.
+template <int SQ, int MOD, bool RECHECK, bool AXIS>
+__global__ void __launch_bounds__(kBlock, AXIS ? 4 : 3) march4_kernel(const __grid_constant__ FrameDesc fd,
+                                                                      const Scratch sc)
 {
     __shared__ int4 stage[RECHECK ? kBlock / 32 : 1][RECHECK ? kQStage : 1];  // recheck entries, per warp
     const int lane = threadIdx.x & 31;
@@ -159,7 +160,7 @@ __global__ void __launch_bounds__(kBlock, 4) march4_kernel(const __grid_constant
         if (tile >= ntiles) break;
         tile = subset_tile(fd, tile);
         LaneStats st;
-        march4_tile<SQ, MOD, RECHECK>(fd, fd.p2, sc, tile, st, stage[RECHECK ? threadIdx.x >> 5 : 0]);
+        march4_tile<SQ, MOD, RECHECK, AXIS>(fd, fd.p2, sc, tile, st, stage[RECHECK ? threadIdx.x >> 5 : 0]);
         flush_lane_stats<false>(sc, st, true);
     }
 }
@@ -340,10 +341,15 @@ cudaError_t launch_passes(const FrameDesc &fd, const Scratch &sc, cudaStream_t s
             // a persistent grid per instantiation: the axis and general forms
             // have different register counts and resident CTAs per SM
             if (fd.axis_slice && fd.march_samples == 2) {
-                static std::atomic<int> g_march4{0};
-                const int cap = num_sms * resident_per_sm(g_march4, march4_kernel<SQ, MOD, RECHECK>);
+                static std::atomic<int> g_march4a{0};
+                const int cap = num_sms * resident_per_sm(g_march4a, march4_kernel<SQ, MOD, RECHECK, true>);
                 const int gm = (int)min((unsigned)cap, (ntiles + 3u) / 4u);
-                march4_kernel<SQ, MOD, RECHECK><<<gm > 0 ? gm : 1, kBlock, 0, st>>>(fd, sc);
+                march4_kernel<SQ, MOD, RECHECK, true><<<gm > 0 ? gm : 1, kBlock, 0, st>>>(fd, sc);
+            } else if (!fd.axis_slice && fd.march_samples == 2) {
+                static std::atomic<int> g_march4g{0};
+                const int cap = num_sms * resident_per_sm(g_march4g, march4_kernel<SQ, MOD, RECHECK, false>);
+                const int gm = (int)min((unsigned)cap, (ntiles + 3u) / 4u);
+                march4_kernel<SQ, MOD, RECHECK, false><<<gm > 0 ? gm : 1, kBlock, 0, st>>>(fd, sc);
             } else if (fd.axis_slice) {
                 const int cap = num_sms * resident_per_sm(g_march2a, march2_kernel<SQ, MOD, RECHECK, true>);
                 const int gm = (int)min((unsigned)cap, (ntiles + 3u) / 4u);

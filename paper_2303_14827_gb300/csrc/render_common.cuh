@@ -687,13 +687,13 @@ __device__ __forceinline__ void march2_tile(const FrameDesc &fd, const PairConst
     warp_push(hitb, make_int4(yb * fd.W + xb, kfb, 0, 0), sc.hits, sc.hit_cap, &sc.ctr->hit_count);
 }
 
-// march2_tile on an axis-aligned slice with two samples of each ray per round
-// (samples k and k + 1, classify_lockstep4_axis): the same per-sample
+// march2_tile with two samples of each ray per round (samples k and k + 1,
+// classify_lockstep4_axis / classify_lockstep4_it1): the same per-sample
 // arithmetic, so the same results, iteration counts and recheck entries.  A
 // sample k + 1 after an inside sample k is classified but not counted or
 // staged, as the one-sample march never reaches it.  Not used for the split
 // march.
-template <int SQ, int MOD, bool RECHECK>
+template <int SQ, int MOD, bool RECHECK, bool AXIS = true>
 __device__ __forceinline__ void march4_tile(const FrameDesc &fd, const PairConsts &P, const Scratch &sc, unsigned tile,
                                             LaneStats &st, int4 *qs = nullptr)
 {
@@ -705,7 +705,10 @@ __device__ __forceinline__ void march4_tile(const FrameDesc &fd, const PairConst
     auto py = [&](int slot) { return ty * fd.tile_h + slot / fd.tile_w; };
     int pixa = 0, pixb = 0;
     bool acta, actb;
-    float2 D[3], tin, dl;
+    // as in march2_tile: zeta_0 = A + t D on an axis slice, else the first
+    // iterate Q0 + s (Q1 + s Q2) with Q0 in D and s = t + dot
+    float2 D[AXIS ? 3 : 8], tin, dl;
+    float2 Q1[AXIS ? 1 : 8], Q2[AXIS ? 1 : 8];
     {
         const int xa = px(lane), ya = py(lane), xb = px(lane + 32), yb = py(lane + 32);
         if (RECHECK) {
@@ -727,9 +730,22 @@ __device__ __forceinline__ void march4_tile(const FrameDesc &fd, const PairConst
         float Da[8], Db[8];
         slice_dir<float>(F, da, Da);
         slice_dir<float>(F, db, Db);
+        if constexpr (AXIS) {
 #pragma unroll
-        for (int i = 0; i < 3; ++i) D[i] = make_float2(Da[i], Db[i]);
-        tin = make_float2(tia, tib);
+            for (int i = 0; i < 3; ++i) D[i] = make_float2(Da[i], Db[i]);
+            tin = make_float2(tia, tib);
+        } else {
+            float Qa[3][8], Qb[3][8], dota, dotb;
+            first_iterate_coeffs<float, SQ>(F.A, Da, F.c, dota, Qa[0], Qa[1], Qa[2]);
+            first_iterate_coeffs<float, SQ>(F.A, Db, F.c, dotb, Qb[0], Qb[1], Qb[2]);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                D[i] = make_float2(Qa[0][i], Qb[0][i]);
+                Q1[i] = make_float2(Qa[1][i], Qb[1][i]);
+                Q2[i] = make_float2(Qa[2][i], Qb[2][i]);
+            }
+            tin = make_float2(vadd(tia, dota), vadd(tib, dotb));
+        }
     }
     const bool boxa = acta, boxb = actb;
     int suma = 0, sumb = 0, maxa = 0, maxb = 0, kfa = -1, kfb = -1;
@@ -744,16 +760,23 @@ __device__ __forceinline__ void march4_tile(const FrameDesc &fd, const PairConst
         const float2 t2 = has2 ? f2fma(f2add(kf, one), dl, tin) : far;
         kf = f2add(kf, two);
         float2 z[8], y[8];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            z[i] = f2fma(t, D[i], P.A[i]);
-            y[i] = f2fma(t2, D[i], P.A[i]);
-        }
         bool ina = acta, inb = actb, ina2 = acta && has2, inb2 = actb && has2, live;
         int ca, cb, ca2, cb2;
         float2 dm, dm2;
-        classify_lockstep4_axis<SQ, MOD, RECHECK>(z, y, P, F.R2, max_iter, ina, inb, ina2, inb2, ca, cb, ca2, cb2,
-                                                  dm, dm2, live);
+        if constexpr (AXIS) {
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                z[i] = f2fma(t, D[i], P.A[i]);
+                y[i] = f2fma(t2, D[i], P.A[i]);
+            }
+            classify_lockstep4_axis<SQ, MOD, RECHECK>(z, y, P, F.R2, max_iter, ina, inb, ina2, inb2, ca, cb, ca2,
+                                                      cb2, dm, dm2, live);
+        } else {
+            first_iterate<float2, 8>(t, D, Q1, Q2, z);
+            first_iterate<float2, 8>(t2, D, Q1, Q2, y);
+            classify_lockstep4_it1<SQ, MOD, RECHECK>(z, y, P, F.R2, max_iter, ina, inb, ina2, inb2, ca, cb, ca2,
+                                                     cb2, dm, dm2, live);
+        }
         if (RECHECK && __any_sync(kFull, fminf(fminf(dm.x, dm.y), fminf(dm2.x, dm2.y)) <= P.margin_t)) {
             // marginal samples in this round (rare): stage sample k's, then sample k + 1's
             const unsigned below = (1u << lane) - 1u;

@@ -7,8 +7,9 @@
 // request with the smallest priority key that still has unclaimed work (the
 // host sets the key: admission order, or arrival time plus the request's
 // estimated cost), claims one work item from it with an atomic add and runs it:
-//   MARCH phase  : one 64-ray tile of the paired march (march2_tile; in the
-//                  recheck mode with the FP64 recheck of its staged samples);
+//   MARCH phase  : one 64-ray tile of the paired march (march4_tile, or
+//                  march2_tile with DQJ_MARCH_SAMPLES=1; in the recheck mode
+//                  with the FP64 recheck of its staged samples);
 //   BISECT phase : 32 hit-list entries (bisect_chunk);
 //   RECHECK phase: 32 recheck-queue entries (recheck_entry), recheck mode only;
 //   FIXUP phase  : one pixel to re-render in FP64 (fixup_pixel), recheck mode.
@@ -142,13 +143,21 @@ __device__ __forceinline__ Scratch load_scratch(const Scratch *src)
 
 }  // namespace
 
-// The work items.  The general-slice march (first-iterate form, ~120
-// registers) and the other phases run behind calls of their own: inlined
-// into one loop with the scheduler and the axis march they spilled
-// registers in the hot loop.  The axis march, the served form's common case,
-// stays inline.
+// The work items run behind calls of their own: the march with two samples
+// per round takes 121-158 registers, and inlined into one loop with the
+// scheduler it spilled registers in the hot loop.  The march takes the form
+// dqj_render takes (fd.march_samples), so a served request's counters equal
+// those of the alone render.
 template <bool RECHECK, bool AXIS>
-__device__ __noinline__ void march_item_general(const FrameDesc &fd, const Scratch &sc, unsigned tile, int4 *stage)
+__device__ __noinline__ void march_item4(const FrameDesc &fd, const Scratch &sc, unsigned tile, int4 *stage)
+{
+    LaneStats st;
+    march4_tile<0, 0, RECHECK, AXIS>(fd, fd.p2, sc, tile, st, stage);
+    flush_lane_stats<false>(sc, st, true);
+}
+
+template <bool RECHECK, bool AXIS>
+__device__ __noinline__ void march_item2(const FrameDesc &fd, const Scratch &sc, unsigned tile, int4 *stage)
 {
     LaneStats st;
     march2_tile<0, 0, RECHECK, AXIS>(fd, fd.p2, sc, tile, st, stage);
@@ -158,13 +167,10 @@ __device__ __noinline__ void march_item_general(const FrameDesc &fd, const Scrat
 template <bool RECHECK, bool AXIS>
 __device__ __forceinline__ void march_item(const FrameDesc &fd, const Scratch &sc, unsigned tile, int4 *stage)
 {
-    if constexpr (AXIS) {
-        LaneStats st;
-        march2_tile<0, 0, RECHECK, true>(fd, fd.p2, sc, tile, st, stage);
-        flush_lane_stats<false>(sc, st, true);
-    } else {
-        march_item_general<RECHECK, false>(fd, sc, tile, stage);
-    }
+    if (fd.march_samples == 2)
+        march_item4<RECHECK, AXIS>(fd, sc, tile, stage);
+    else
+        march_item2<RECHECK, AXIS>(fd, sc, tile, stage);
 }
 
 template <bool RECHECK>
@@ -198,7 +204,7 @@ __device__ __forceinline__ unsigned claim(unsigned long long *ctr, unsigned tota
     return c < total ? (unsigned)c : ~0u;
 }
 
-__global__ void __launch_bounds__(kBlock, 4) serve_kernel(ServeCtl ctl)
+__global__ void __launch_bounds__(kBlock, 3) serve_kernel(ServeCtl ctl)
 {
     __shared__ FrameDesc s_fd[kBlock / 32];
     __shared__ int4 s_stage[kBlock / 32][kQStage];  // recheck entries of a march tile, per warp

@@ -41,6 +41,9 @@ def scenes_list():
     # FP32 frames with more tiles than resident warps take the unsplit march
     out.append(scenes.default_scene(width=640, height=480, precision=scenes.PRECISION_FP32))
     out.append(scenes.default_scene(width=641, height=483, march_steps=255, precision=scenes.PRECISION_FP32))
+    for prec in (scenes.PRECISION_FP32, scenes.PRECISION_FP32_RECHECK):
+        out.append(scenes.default_scene(width=640, height=480, march_steps=255, precision=prec,
+                                        slice_basis=scenes.random_slice_frame(rng)))
     return out
 
 

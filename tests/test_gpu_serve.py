@@ -3,7 +3,7 @@ limits, slice frames and both FP32 modes (plain, and FP32 + FP64 recheck) run
 together in the persistent launch (other precisions and modes as frames on the
 serving stream).  Every result must be
 identical to rendering the same request alone with dqj_render, whatever else was
-in the mix (the recheck counter within 0.1 %, see assert_same).  Budget-limited admission and a long stream of small requests are
+in the mix.  Budget-limited admission and a long stream of small requests are
 covered too."""
 import time
 
@@ -36,18 +36,10 @@ def run_served(ctx, reqs, timeout=60.0):
 
 
 def assert_same(a, b, s, what):
-    """Planes bit for bit and every counter equal, except that the recheck
-    counter may differ by 0.1 %: on an axis slice dqj_render marches two
-    samples of each ray per round and the served launch one, and a sample is
-    also flagged when a modulus taken after its escape, while other samples of
-    the warp still iterate, comes within the band."""
     x, y = to_numpy(a, s["width"], s["height"]), to_numpy(b, s["width"], s["height"])
     for k in ("iter", "depth", "normal", "rgba"):
         assert np.array_equal(x[k], y[k]), (what, k)
-    sa, sb = binding.stats_dict(a["stats"]), binding.stats_dict(b["stats"])
-    ra, rb = sa.pop("rechecks"), sb.pop("rechecks")
-    assert sa == sb, what
-    assert abs(ra - rb) <= max(2, ra // 1000), (what, ra, rb)
+    assert binding.stats_dict(a["stats"]) == binding.stats_dict(b["stats"]), what
 
 
 def mixed_requests():
