@@ -193,6 +193,26 @@ __global__ void __launch_bounds__(kBlock, AXIS ? 5 : 4) march2_split_kernel(cons
     }
 }
 
+// march2_split_kernel with two samples of each ray per round (march4_tile).
+template <int SQ, int MOD, bool AXIS>
+__global__ void __launch_bounds__(kBlock, AXIS ? 4 : 3) march4_split_kernel(const __grid_constant__ FrameDesc fd,
+                                                                            const Scratch sc)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned ntiles = subset_tiles(fd, (unsigned)fd.tiles_x * (unsigned)fd.tiles_y);
+    const unsigned items = ntiles * (unsigned)fd.k_split;
+    for (;;) {
+        unsigned item = 0;
+        if (lane == 0) item = atomicAdd(&sc.ctr->tile_next, 1u);
+        item = __shfl_sync(kFull, item, 0);
+        if (item >= items) break;
+        const unsigned r = item / ntiles, tile = subset_tile(fd, item % ntiles);
+        const int kb = (int)r * fd.k_chunk, ke = min(kb + fd.k_chunk, fd.N + 1);
+        LaneStats st;
+        march4_tile<SQ, MOD, false, AXIS, true>(fd, fd.p2, sc, tile, st, nullptr, kb, ke);
+    }
+}
+
 // Per pixel: the ranges of the split march in sample order up to the first
 // with an inside sample give the pixel's result (a miss's largest escape count,
 // or the hit's first inside sample for the bisection pass) and its iterations
@@ -324,7 +344,18 @@ cudaError_t launch_passes(const FrameDesc &fd, const Scratch &sc, cudaStream_t s
         if (fd.march_variant == 1 && fd.k_split > 1) {
             static std::atomic<int> g_sa{0}, g_sg{0}, g_mg{0};
             const unsigned items = ntiles * (unsigned)fd.k_split;
-            if (fd.axis_slice) {
+            if (fd.march_samples == 2) {
+                static std::atomic<int> g_s4a{0}, g_s4g{0};
+                if (fd.axis_slice) {
+                    const int cap = num_sms * resident_per_sm(g_s4a, march4_split_kernel<SQ, MOD, true>);
+                    march4_split_kernel<SQ, MOD, true>
+                        <<<(int)min((unsigned)cap, (items + 3u) / 4u), kBlock, 0, st>>>(fd, sc);
+                } else {
+                    const int cap = num_sms * resident_per_sm(g_s4g, march4_split_kernel<SQ, MOD, false>);
+                    march4_split_kernel<SQ, MOD, false>
+                        <<<(int)min((unsigned)cap, (items + 3u) / 4u), kBlock, 0, st>>>(fd, sc);
+                }
+            } else if (fd.axis_slice) {
                 const int cap = num_sms * resident_per_sm(g_sa, march2_split_kernel<SQ, MOD, true>);
                 march2_split_kernel<SQ, MOD, true><<<(int)min((unsigned)cap, (items + 3u) / 4u), kBlock, 0, st>>>(fd, sc);
             } else {
@@ -416,7 +447,10 @@ int march_split(const FrameDesc &fd, int num_sms)
         if (n <= 1) return 1;
         return (int)std::min<long>(std::min<long>(n, 64), (long)fd.N + 1);
     }
-    const long long warps = (long long)num_sms * resident_per_sm(g_occ, march2_split_kernel<0, 0, true>) * (kBlock / 32);
+    static std::atomic<int> g_occ4{0};
+    const int per_sm = fd.march_samples == 2 ? resident_per_sm(g_occ4, march4_split_kernel<0, 0, true>)
+                                             : resident_per_sm(g_occ, march2_split_kernel<0, 0, true>);
+    const long long warps = (long long)num_sms * per_sm * (kBlock / 32);
     const long long tiles = subset_tiles(fd, (unsigned)fd.tiles_x * (unsigned)fd.tiles_y);
     if (tiles >= warps || tiles == 0) return 1;
     // about four waves of items: later waves skip the rays earlier ranges hit

@@ -691,11 +691,11 @@ __device__ __forceinline__ void march2_tile(const FrameDesc &fd, const PairConst
 // classify_lockstep4_axis / classify_lockstep4_it1): the same per-sample
 // arithmetic, so the same results, iteration counts and recheck entries.  A
 // sample k + 1 after an inside sample k is classified but not counted or
-// staged, as the one-sample march never reaches it.  Not used for the split
-// march.
-template <int SQ, int MOD, bool RECHECK, bool AXIS = true>
+// staged, as the one-sample march never reaches it.  SPLIT: samples [kb, ke)
+// of each ray with the range's partial result, as in march2_tile.
+template <int SQ, int MOD, bool RECHECK, bool AXIS = true, bool SPLIT = false>
 __device__ __forceinline__ void march4_tile(const FrameDesc &fd, const PairConsts &P, const Scratch &sc, unsigned tile,
-                                            LaneStats &st, int4 *qs = nullptr)
+                                            LaneStats &st, int4 *qs = nullptr, int kb = 0, int ke = 0)
 {
     const FrameT<float> &F = fd.f;
     const int lane = threadIdx.x & 31;
@@ -704,7 +704,7 @@ __device__ __forceinline__ void march4_tile(const FrameDesc &fd, const PairConst
     auto px = [&](int slot) { return tx * fd.tile_w + slot % fd.tile_w; };
     auto py = [&](int slot) { return ty * fd.tile_h + slot / fd.tile_w; };
     int pixa = 0, pixb = 0;
-    bool acta, actb;
+    bool acta, actb, skipa = false, skipb = false;
     // as in march2_tile: zeta_0 = A + t D on an axis slice, else the first
     // iterate Q0 + s (Q1 + s Q2) with Q0 in D and s = t + dot
     float2 D[AXIS ? 3 : 8], tin, dl;
@@ -720,6 +720,13 @@ __device__ __forceinline__ void march4_tile(const FrameDesc &fd, const PairConst
         float tia = 0.f, toa = 0.f, tib = 0.f, tob = 0.f;
         acta = va && camera_clip<float>(F, fd.W, fd.H, xa, ya, da, tia, toa);
         actb = vb && camera_clip<float>(F, fd.W, fd.H, xb, yb, db, tib, tob);
+        if constexpr (SPLIT) {
+            const unsigned r = (unsigned)(kb / fd.k_chunk);
+            skipa = va && __ldcg(sc.part_hit + ya * fd.W + xa) < r;
+            skipb = vb && __ldcg(sc.part_hit + yb * fd.W + xb) < r;
+            acta = acta && !skipa;
+            actb = actb && !skipb;
+        }
         if (!acta) tia = toa = 0.f;
         if (!actb) tib = tob = 0.f;
         dl = make_float2((toa - tia) / (float)N, (tob - tib) / (float)N);
@@ -750,11 +757,11 @@ __device__ __forceinline__ void march4_tile(const FrameDesc &fd, const PairConst
     const bool boxa = acta, boxb = actb;
     int suma = 0, sumb = 0, maxa = 0, maxb = 0, kfa = -1, kfb = -1;
     int qn = 0;  // staged recheck entries (warp-uniform)
-    const int k1 = N + 1;
-    float2 kf = make_float2(0.f, 0.f);
+    const int k0 = SPLIT ? kb : 0, k1 = SPLIT ? ke : N + 1;
+    float2 kf = make_float2((float)k0, (float)k0);
     const float2 one = make_float2(1.f, 1.f), two = make_float2(2.f, 2.f), far = make_float2(kFarT, kFarT);
     bool more = __any_sync(kFull, acta || actb);
-    for (int k = 0; k < k1 && more; k += 2) {
+    for (int k = k0; k < k1 && more; k += 2) {
         const bool has2 = k + 1 < k1;  // warp-uniform: the last round of an even count has one sample
         const float2 t = f2fma(kf, dl, tin);
         const float2 t2 = has2 ? f2fma(f2add(kf, one), dl, tin) : far;
@@ -827,7 +834,25 @@ __device__ __forceinline__ void march4_tile(const FrameDesc &fd, const PairConst
     }
     if (RECHECK && qn > 0) recheck_staged<SQ, MOD>(fd, sc, qs, qn);
     const bool hita = kfa >= 0, hitb = kfb >= 0;
-    const int nesca = hita ? kfa : k1, nescb = hitb ? kfb : k1;
+    const int nesca = (hita ? kfa : k1) - k0, nescb = (hitb ? kfb : k1) - k0;
+    if constexpr (SPLIT) {  // this range's partial result per ray (see march_merge_kernel)
+        const int xa = px(lane), ya = py(lane), xb = px(lane + 32), yb = py(lane + 32);
+        const unsigned r = (unsigned)(kb / fd.k_chunk);
+        const int64_t npx = (int64_t)fd.W * fd.H, base = (int64_t)r * npx;
+        if (xa < fd.W && ya < fd.H && !skipa) {
+            const int pa = ya * fd.W + xa;
+            sc.part[base + pa] = boxa ? make_int4(kfa, suma + nesca, maxa + 1, nesca + (hita ? 1 : 0))
+                                      : make_int4(-1, 0, 0, 0);
+            if (hita) atomicMin(sc.part_hit + pa, r);
+        }
+        if (xb < fd.W && yb < fd.H && !skipb) {
+            const int pb = yb * fd.W + xb;
+            sc.part[base + pb] = boxb ? make_int4(kfb, sumb + nescb, maxb + 1, nescb + (hitb ? 1 : 0))
+                                      : make_int4(-1, 0, 0, 0);
+            if (hitb) atomicMin(sc.part_hit + pb, r);
+        }
+        return;
+    }
     st.iters += (boxa ? suma + nesca : 0) + (boxb ? sumb + nescb : 0);
     st.samples += (boxa ? nesca + (hita ? 1 : 0) : 0) + (boxb ? nescb + (hitb ? 1 : 0) : 0);
     st.hits += (hita ? 1 : 0) + (hitb ? 1 : 0);
