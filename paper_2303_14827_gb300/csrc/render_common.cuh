@@ -762,7 +762,7 @@ __device__ __forceinline__ void march4_tile(const FrameDesc &fd, const PairConst
     const float2 one = make_float2(1.f, 1.f), two = make_float2(2.f, 2.f), far = make_float2(kFarT, kFarT);
     bool more = __any_sync(kFull, acta || actb);
     for (int k = k0; k < k1 && more; k += 2) {
-        const bool has2 = k + 1 < k1;  // warp-uniform: the last round of an even count has one sample
+        const bool has2 = k + 1 < k1;  // warp-uniform: an odd number of samples ends in a round of one
         const float2 t = f2fma(kf, dl, tin);
         const float2 t2 = has2 ? f2fma(f2add(kf, one), dl, tin) : far;
         kf = f2add(kf, two);
